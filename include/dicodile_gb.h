@@ -1,0 +1,193 @@
+/*
+ * dicodile_gb.h -- C ABI of the GB300 (sm_103a) convolutional sparse coding
+ * library: locally greedy coordinate descent (LGCD) with the soft-lock rule of
+ * DiCoDiLe, and the dictionary-update statistics and step that follow it.
+ *
+ * Problem (Section 2, Eq. csc / Eq. cdl):
+ *     min_Z  1/2 || X - Z * D ||_2^2 + lambda ||Z||_1,
+ *     min_D  1/2 || X - Z * D ||_2^2   s.t. ||D_k||_2 <= 1.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Shapes: d convolutional dimensions (1 or 2), P channels, K atoms, signal
+ *    size T, atom size L.  For d == 1 only T[0] and L[0] are used and T[1],
+ *    L[1] must be 1.  For d == 2, index 0 is the row (slow) axis.
+ *  - The activation domain is the "valid" one: Tz_i = T_i - L_i + 1, so that
+ *    X = Z * D covers the signal exactly.
+ *  - Layouts are dense, row-major, fp32 unless stated:
+ *        X    [P][T0][T1]          D    [K][P][L0][L1]
+ *        Z    [K][Tz0][Tz1]        beta [K][Tz0][Tz1]
+ *        dtd  [K][K][2L0-1][2L1-1] phi  [K][K][2L0-1][2L1-1]
+ *        psi  [K][P][L0][L1]
+ *    (for d == 1 drop the size-1 axes: X [P][T], D [K][P][L], ...).
+ *    dtd[k][k2][delta + L - 1] = sum_p sum_tau D_kp[tau] D_k2p[tau + delta].
+ *  - All array pointers are DEVICE pointers owned by the caller; the library
+ *    never allocates device memory.  Scratch space is a caller-owned device
+ *    buffer of at least csc_workspace_size() bytes.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream).  Calls that return a host scalar or a stats struct synchronise
+ *    that stream before returning; this is stated per call.
+ *  - Every call returns a status code (CSC_OK == 0).  On CSC_ERR_INVALID
+ *    nothing was enqueued.  On CSC_ERR_CUDA the CUDA error is also available
+ *    from csc_last_cuda_error().
+ */
+#ifndef DICODILE_GB_H
+#define DICODILE_GB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CSC_API __attribute__((visibility("default")))
+#else
+#define CSC_API
+#endif
+
+typedef void *csc_stream_t; /* a cudaStream_t */
+
+enum csc_status {
+    CSC_OK = 0,
+    CSC_ERR_INVALID = 1,       /* bad shape, null pointer, L > T, bad option   */
+    CSC_ERR_CUDA = 2,          /* a CUDA runtime call failed                   */
+    CSC_NOT_CONVERGED = 3,     /* max_updates reached before max|dZ| < tol     */
+    CSC_ERR_TIMEOUT = 4,       /* a device-side wait hit its time limit        */
+    CSC_ERR_DIVERGED = 5,      /* ||Z||_inf > min_k 50 / ||D_k||_inf (Sec. 5.1) */
+    CSC_ERR_UNIMPLEMENTED = 6, /* shape/option combination not supported       */
+    CSC_ERR_WORKSPACE = 7      /* workspace too small for this call            */
+};
+
+enum csc_mode {
+    CSC_MODE_ASYNC = 0,   /* tiles update asynchronously; border updates pass the soft-lock test */
+    CSC_MODE_PHASED = 1,  /* deterministic checkerboard phases (for testing)                     */
+    CSC_MODE_NOLOCK = 2   /* asynchronous without the soft-lock (ablation only)                   */
+};
+
+typedef struct {
+    int d;     /* 1 or 2                                  */
+    int P;     /* channels                                */
+    int K;     /* atoms                                   */
+    int T[2];  /* signal size                             */
+    int L[2];  /* atom size                               */
+} csc_shape;
+
+typedef struct {
+    int tile[2];          /* worker tile per dimension (0 = planned automatically)        */
+    int sub[2];           /* LGCD sub-domain per dimension (0 = 2 L_i, Section 3)          */
+    int mode;             /* enum csc_mode                                                 */
+    int max_workers;      /* upper bound on the number of tiles (0 = all co-resident)      */
+    long long max_updates;/* stop with CSC_NOT_CONVERGED after this many (0 = no limit)    */
+    double timeout_s;     /* device wall-clock limit of one solve launch (0 = 30 s)        */
+    int beta_refresh;     /* re-solves allowed after recomputing beta from scratch (>= 0)  */
+    int divergence_guard; /* 1 = stop with CSC_ERR_DIVERGED when the Section 5.1 bound hits */
+    int warm_start;       /* 1 = Z and beta on entry are a consistent starting point        */
+} csc_solve_opts;
+
+typedef struct {
+    long long updates;           /* accepted coordinate updates                          */
+    long long iterations;        /* sub-domain iterations over all workers               */
+    long long rejected_softlock; /* border candidates rejected by the soft-lock test     */
+    long long skipped_subtol;    /* iterations whose best |dZ| was below tol             */
+    long long messages;          /* neighbour notifications (k0, s0, dZ) sent            */
+    long long refresh_rounds;    /* beta recomputations from scratch                     */
+    int workers;                 /* tiles (one CTA each)                                 */
+    int tiles[2];                /* tile grid                                            */
+    int tile_size[2];            /* full tile size                                       */
+    double max_dz_final;         /* max |dZ| on a freshly recomputed beta (final KKT)    */
+    double objective;            /* 1/2||X - Z*D||^2 + lambda||Z||_1, FP64 accumulation   */
+    long long nnz;               /* nonzeros of Z at the end                             */
+    double kernel_ms;            /* device time of the LGCD launches (CUDA events)       */
+    int status;                  /* the returned status                                  */
+} csc_solve_stats;
+
+/* Default options: automatic tiling, sub-domains of 2L, ASYNC mode, refresh 2. */
+CSC_API void csc_default_opts(csc_solve_opts *opts);
+
+/* Bytes of device workspace needed by csc_lgcd_solve, csc_objective and
+ * cdl_dict_stats / cdl_dict_update for `shape` under `opts` (opts may be NULL
+ * for the defaults).  Host-only; does not touch the GPU beyond querying the
+ * device properties of the current device. */
+CSC_API int csc_workspace_size(const csc_shape *shape, const csc_solve_opts *opts, size_t *bytes);
+
+/* beta = D~ * X and the atom cross-correlation table (Alg. 1 initialisation,
+ * Eq. beta_update table, Section 3; lambda_max of Section 2).
+ *   X [P][T] in, D [K][P][L] in, beta [K][Tz] out, dtd [K][K][2L-1] out.
+ *   beta_k[s] = sum_p sum_tau D_kp[tau] X_p[s + tau]  (cross-correlation).
+ *   lambda_max_out: host pointer, may be NULL; when given, receives
+ *   max |beta| and the call synchronises `stream`.
+ *   workspace: device scratch of csc_workspace_size() bytes (holds the
+ *   max |beta| reduction). */
+CSC_API int csc_init_beta(const csc_shape *shape, const float *X, const float *D, float *beta,
+                  float *dtd, double *lambda_max_out, void *workspace, size_t workspace_bytes,
+                  csc_stream_t stream);
+
+/* Convolutional sparse coding by LGCD (Alg. 1) over a grid of worker tiles
+ * with the soft-lock rule (Alg. 3, Eq. soft_lock), one persistent CTA per tile.
+ *   X, D     : the problem (needed to recompute beta from scratch at the end).
+ *   dtd      : table from csc_init_beta.
+ *   beta     : in: beta for the starting Z (from csc_init_beta when Z = 0);
+ *              out: beta recomputed from scratch for the returned Z.
+ *   Z        : out (zeroed by the call unless opts->warm_start).
+ *   lambda   : absolute regularisation (not a fraction of lambda_max).
+ *   tol      : eps of Alg. 1: the solve stops when no coordinate can change
+ *              by tol or more; this is then re-checked on a fresh beta
+ *              (stats->max_dz_final) and the solve resumes if it fails.
+ *   stats    : host pointer, may be NULL.
+ * Synchronises `stream` before returning (the status comes from the device). */
+CSC_API int csc_lgcd_solve(const csc_shape *shape, const float *X, const float *D, const float *dtd,
+                   float *beta, float *Z, float lambda, float tol, const csc_solve_opts *opts,
+                   void *workspace, size_t workspace_bytes, csc_solve_stats *stats,
+                   csc_stream_t stream);
+
+/* 1/2 ||X - Z*D||^2 + lambda ||Z||_1 accumulated in FP64 (Eq. csc).
+ * objective_out is a host pointer; synchronises `stream`. */
+CSC_API int csc_objective(const csc_shape *shape, const float *X, const float *D, const float *Z,
+                  double lambda, double *objective_out, void *workspace,
+                  size_t workspace_bytes, csc_stream_t stream);
+
+/* Sufficient statistics of the dictionary update (Section 4.2, Eq. phi):
+ *   phi_{k,k2}[delta] = sum_s Z_k[s] Z_k2[s + delta],  delta in prod ]-L_i, L_i[
+ *   psi_kp[tau]       = sum_s Z_k[s] X_p[s + tau],     tau in Theta
+ * computed from the nonzeros of Z.  phi [K][K][2L-1], psi [K][P][L] out.
+ * Asynchronous. */
+CSC_API int cdl_dict_stats(const csc_shape *shape, const float *Z, const float *X, float *phi,
+                   float *psi, void *workspace, size_t workspace_bytes, csc_stream_t stream);
+
+/* Dictionary step (Alg. 2): projected gradient descent on D with Armijo
+ * backtracking, gradient phi * D - psi, projection D_k /= max(1, ||D_k||_2).
+ * The first step is 1 / max_k sum_k2 sum_delta |phi_{k,k2}[delta]|, each later
+ * iteration starts from twice the last accepted step; at most max_iter
+ * iterations, stop when ||D+ - D|| < tol ||D||.
+ *   D: in/out.  x_sqnorm: ||X||_2^2.  objective_out: host pointer (may be
+ *   NULL) receiving F(D) = 1/2||X - Z*D||^2 at the end (FP64);
+ *   iterations_out: host pointer (may be NULL).
+ * Synchronises `stream` when either output pointer is given. */
+CSC_API int cdl_dict_update(const csc_shape *shape, const float *phi, const float *psi,
+                    double x_sqnorm, float *D, int max_iter, double tol,
+                    double *objective_out, int *iterations_out, void *workspace,
+                    size_t workspace_bytes, csc_stream_t stream);
+
+/* FP64 variants of csc_init_beta and csc_lgcd_solve (same layouts, double
+ * elements).  They exist to verify the tiled schedule exactly against an FP64
+ * reference; they are slow on GB300, whose FP64 rate is low. */
+CSC_API int csc_init_beta_f64(const csc_shape *shape, const double *X, const double *D, double *beta,
+                      double *dtd, double *lambda_max_out, void *workspace,
+                      size_t workspace_bytes, csc_stream_t stream);
+CSC_API int csc_lgcd_solve_f64(const csc_shape *shape, const double *X, const double *D,
+                       const double *dtd, double *beta, double *Z, double lambda, double tol,
+                       const csc_solve_opts *opts, void *workspace, size_t workspace_bytes,
+                       csc_solve_stats *stats, csc_stream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+CSC_API const char *csc_status_string(int status);
+
+/* The last CUDA error code seen by this library on this thread (0 if none). */
+CSC_API int csc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DICODILE_GB_H */

@@ -1,0 +1,308 @@
+"""Python binding of the GB300 CSC library (``include/dicodile_gb.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``lib/libdicodile_gb.so``.  Tensors are torch CUDA tensors (float32,
+or float64 for the ``_f64`` calls), contiguous, laid out as the header states:
+
+  1-D: X (P, T),      D (K, P, L),      Z / beta (K, T - L + 1)
+  2-D: X (P, T0, T1), D (K, P, L0, L1), Z / beta (K, T0 - L0 + 1, T1 - L1 + 1)
+
+Calls are enqueued on the current torch stream.  If the library is missing
+the functions raise; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libdicodile_gb.so")
+
+CSC_OK, CSC_ERR_INVALID, CSC_ERR_CUDA, CSC_NOT_CONVERGED = 0, 1, 2, 3
+CSC_ERR_TIMEOUT, CSC_ERR_DIVERGED, CSC_ERR_UNIMPLEMENTED, CSC_ERR_WORKSPACE = 4, 5, 6, 7
+MODE_ASYNC, MODE_PHASED, MODE_NOLOCK = 0, 1, 2
+
+
+class Shape(C.Structure):
+    _fields_ = [("d", C.c_int), ("P", C.c_int), ("K", C.c_int),
+                ("T", C.c_int * 2), ("L", C.c_int * 2)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tile", C.c_int * 2), ("sub", C.c_int * 2), ("mode", C.c_int),
+                ("max_workers", C.c_int), ("max_updates", C.c_longlong),
+                ("timeout_s", C.c_double), ("beta_refresh", C.c_int),
+                ("divergence_guard", C.c_int), ("warm_start", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("updates", C.c_longlong), ("iterations", C.c_longlong),
+                ("rejected_softlock", C.c_longlong), ("skipped_subtol", C.c_longlong),
+                ("messages", C.c_longlong), ("refresh_rounds", C.c_longlong),
+                ("workers", C.c_int), ("tiles", C.c_int * 2), ("tile_size", C.c_int * 2),
+                ("max_dz_final", C.c_double), ("objective", C.c_double),
+                ("nnz", C.c_longlong), ("kernel_ms", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+class CscError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = status_string(status) if _lib is not None else str(status)
+        if status == CSC_ERR_CUDA and _lib is not None:
+            msg += f" (cudaError {_lib.csc_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run paper_1901_09235_gb300.build)")
+    lib = C.CDLL(LIB_PATH)
+    p, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    S, O, ST = C.POINTER(Shape), C.POINTER(SolveOpts), C.POINTER(SolveStats)
+    sig = {
+        "csc_default_opts": (None, [O]),
+        "csc_workspace_size": (i, [S, O, C.POINTER(sz)]),
+        "csc_init_beta": (i, [S, p, p, p, p, C.POINTER(d), p, sz, p]),
+        "csc_init_beta_f64": (i, [S, p, p, p, p, C.POINTER(d), p, sz, p]),
+        "csc_lgcd_solve": (i, [S, p, p, p, p, p, C.c_float, C.c_float, O, p, sz, ST, p]),
+        "csc_lgcd_solve_f64": (i, [S, p, p, p, p, p, d, d, O, p, sz, ST, p]),
+        "csc_objective": (i, [S, p, p, p, d, C.POINTER(d), p, sz, p]),
+        "cdl_dict_stats": (i, [S, p, p, p, p, p, sz, p]),
+        "cdl_dict_update": (i, [S, p, p, d, p, i, d, C.POINTER(d), C.POINTER(i), p, sz, p]),
+        "csc_status_string": (C.c_char_p, [i]),
+        "csc_last_cuda_error": (i, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().csc_status_string(int(status)).decode()
+
+
+def _check(rc: int, where: str, soft=()):
+    if rc != CSC_OK and rc not in soft:
+        raise CscError(rc, where)
+    return rc
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def make_shape(X_shape, D_shape) -> Shape:
+    """csc_shape from the tensor shapes of X and D."""
+    s = Shape()
+    if len(X_shape) == 2:
+        P, T = X_shape
+        K, P2, L = D_shape
+        s.d, s.P, s.K = 1, P, K
+        s.T[0], s.T[1], s.L[0], s.L[1] = T, 1, L, 1
+    elif len(X_shape) == 3:
+        P, T0, T1 = X_shape
+        K, P2, L0, L1 = D_shape
+        s.d, s.P, s.K = 2, P, K
+        s.T[0], s.T[1], s.L[0], s.L[1] = T0, T1, L0, L1
+    else:
+        raise ValueError("X must be (P, T) or (P, T0, T1)")
+    if P2 != P:
+        raise ValueError("D and X disagree on P")
+    return s
+
+
+def z_shape(s: Shape):
+    if s.d == 1:
+        return (s.K, s.T[0] - s.L[0] + 1)
+    return (s.K, s.T[0] - s.L[0] + 1, s.T[1] - s.L[1] + 1)
+
+
+def tab_shape(s: Shape):
+    if s.d == 1:
+        return (s.K, s.K, 2 * s.L[0] - 1)
+    return (s.K, s.K, 2 * s.L[0] - 1, 2 * s.L[1] - 1)
+
+
+def default_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    load().csc_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k in ("tile", "sub"):
+            arr = getattr(o, k)
+            vals = list(v) + [0] * (2 - len(v))
+            arr[0], arr[1] = vals[0], vals[1]
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def workspace_size(shape: Shape, opts: SolveOpts | None = None) -> int:
+    n = C.c_size_t(0)
+    _check(load().csc_workspace_size(C.byref(shape), C.byref(opts) if opts else None, C.byref(n)),
+           "csc_workspace_size")
+    return int(n.value)
+
+
+def workspace(shape: Shape, opts: SolveOpts | None = None, device=None):
+    """A caller-owned device workspace (uint8 tensor) for ``shape``."""
+    import torch
+    return torch.empty(workspace_size(shape, opts), dtype=torch.uint8, device=device or "cuda")
+
+
+def csc_init_beta(X, D, beta=None, dtd=None, ws=None, stream=None, want_lambda_max=True):
+    """beta = D~ * X, the D^T D table and lambda_max (csc_init_beta)."""
+    import torch
+    f64 = X.dtype == torch.float64
+    dt = torch.float64 if f64 else torch.float32
+    _need(X, dt, "X")
+    _need(D, dt, "D")
+    s = make_shape(tuple(X.shape), tuple(D.shape))
+    if beta is None:
+        beta = torch.empty(z_shape(s), dtype=dt, device=X.device)
+    if dtd is None:
+        dtd = torch.empty(tab_shape(s), dtype=dt, device=X.device)
+    if ws is None:
+        ws = workspace(s, device=X.device)
+    lm = C.c_double(0.0)
+    fn = load().csc_init_beta_f64 if f64 else load().csc_init_beta
+    _check(fn(C.byref(s), _ptr(X), _ptr(D), _ptr(beta), _ptr(dtd),
+              C.byref(lm) if want_lambda_max else None, _ptr(ws), ws.numel(), _stream(stream)),
+           "csc_init_beta")
+    return beta, dtd, (lm.value if want_lambda_max else None)
+
+
+def csc_lgcd_solve(X, D, dtd, beta, lam: float, tol: float, Z=None, opts: SolveOpts | None = None,
+                   ws=None, stream=None):
+    """LGCD with soft-locks (csc_lgcd_solve).  beta is updated in place.
+    Returns (Z, stats dict).  NOT_CONVERGED / DIVERGED are reported in
+    stats['status']; other failures raise CscError."""
+    import torch
+    f64 = X.dtype == torch.float64
+    dt = torch.float64 if f64 else torch.float32
+    for t, n in ((X, "X"), (D, "D"), (dtd, "dtd"), (beta, "beta")):
+        _need(t, dt, n)
+    s = make_shape(tuple(X.shape), tuple(D.shape))
+    if Z is None:
+        Z = torch.empty(z_shape(s), dtype=dt, device=X.device)
+    _need(Z, dt, "Z")
+    if opts is None:
+        opts = default_opts()
+    if ws is None:
+        ws = workspace(s, opts, device=X.device)
+    st = SolveStats()
+    fn = load().csc_lgcd_solve_f64 if f64 else load().csc_lgcd_solve
+    rc = fn(C.byref(s), _ptr(X), _ptr(D), _ptr(dtd), _ptr(beta), _ptr(Z), lam, tol, C.byref(opts),
+            _ptr(ws), ws.numel(), C.byref(st), _stream(stream))
+    _check(rc, "csc_lgcd_solve", soft=(CSC_NOT_CONVERGED, CSC_ERR_DIVERGED))
+    return Z, st.as_dict()
+
+
+def csc_objective(X, D, Z, lam: float, ws=None, stream=None) -> float:
+    import torch
+    for t, n in ((X, "X"), (D, "D"), (Z, "Z")):
+        _need(t, torch.float32, n)
+    s = make_shape(tuple(X.shape), tuple(D.shape))
+    if ws is None:
+        ws = workspace(s, device=X.device)
+    out = C.c_double(0.0)
+    _check(load().csc_objective(C.byref(s), _ptr(X), _ptr(D), _ptr(Z), float(lam), C.byref(out),
+                                _ptr(ws), ws.numel(), _stream(stream)), "csc_objective")
+    return out.value
+
+
+def cdl_dict_stats(Z, X, D_shape, phi=None, psi=None, ws=None, stream=None):
+    """phi = Z~ * Z on Phi and psi = Z~ * X on Theta (cdl_dict_stats)."""
+    import torch
+    _need(Z, torch.float32, "Z")
+    _need(X, torch.float32, "X")
+    s = make_shape(tuple(X.shape), tuple(D_shape))
+    if phi is None:
+        phi = torch.empty(tab_shape(s), dtype=torch.float32, device=X.device)
+    if psi is None:
+        psi = torch.empty(tuple(D_shape), dtype=torch.float32, device=X.device)
+    if ws is None:
+        ws = workspace(s, device=X.device)
+    _check(load().cdl_dict_stats(C.byref(s), _ptr(Z), _ptr(X), _ptr(phi), _ptr(psi), _ptr(ws),
+                                 ws.numel(), _stream(stream)), "cdl_dict_stats")
+    return phi, psi
+
+
+def cdl_dict_update(phi, psi, x_sqnorm: float, D, X_shape, max_iter: int = 50, tol: float = 1e-8,
+                    ws=None, stream=None):
+    """PGD + Armijo on D in place (cdl_dict_update).  Returns (F, iterations)."""
+    import torch
+    for t, n in ((phi, "phi"), (psi, "psi"), (D, "D")):
+        _need(t, torch.float32, n)
+    s = make_shape(tuple(X_shape), tuple(D.shape))
+    if ws is None:
+        ws = workspace(s, device=D.device)
+    f = C.c_double(0.0)
+    it = C.c_int(0)
+    _check(load().cdl_dict_update(C.byref(s), _ptr(phi), _ptr(psi), float(x_sqnorm), _ptr(D),
+                                  int(max_iter), float(tol), C.byref(f), C.byref(it), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "cdl_dict_update")
+    return f.value, it.value
+
+
+@dataclass
+class Problem:
+    """Device-resident buffers of one CSC problem (inputs stay in HBM)."""
+    X: object
+    D: object
+    shape: Shape
+    ws: object
+    beta: object = None
+    dtd: object = None
+    Z: object = None
+    phi: object = None
+    psi: object = None
+
+    @classmethod
+    def create(cls, X, D, opts=None):
+        import torch
+        s = make_shape(tuple(X.shape), tuple(D.shape))
+        p = cls(X=X, D=D, shape=s, ws=workspace(s, opts, device=X.device))
+        p.beta = torch.empty(z_shape(s), dtype=X.dtype, device=X.device)
+        p.Z = torch.empty_like(p.beta)
+        p.dtd = torch.empty(tab_shape(s), dtype=X.dtype, device=X.device)
+        p.phi = torch.empty(tab_shape(s), dtype=torch.float32, device=X.device)
+        p.psi = torch.empty(tuple(D.shape), dtype=torch.float32, device=X.device)
+        return p

@@ -1,0 +1,253 @@
+// corr.cu -- dense correlations of the CSC path on CUDA cores:
+//   beta_k[s] = sum_p sum_tau D_kp[tau] S_p[s + tau]   (Alg. 1 initialisation
+//               with S = X; the from-scratch recomputation of beta with
+//               S = X - Z*D plus ||D_k||^2 Z_k, Section 3),
+//   C[k][k2][delta] = sum_p sum_tau D_kp[tau] D_k2p[tau + delta]
+//               (the table of Eq. beta_update),
+//   ||D_k||^2 in FP64 and max |D_k| (Section 5.1 divergence bound).
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace csc {
+
+template <typename real>
+struct CorrArgs {
+    const real *S;      // P x T0 x T1
+    const real *Wt;     // K x P x L0 x L1
+    real *out;          // K x Z0 x Z1
+    const real *Zc;     // refresh: current Z (K x Z0 x Z1)
+    const double *nrm;  // refresh: ||D_k||^2
+    real lambda;
+    unsigned long long *bits;  // init: max |beta|; refresh: max |dZ|
+    int P, K, T0, T1, L0, L1, Z0, Z1;
+};
+
+enum { EPI_INIT = 0, EPI_REFRESH = 1 };
+
+// One CTA computes a TR x TC block of positions for KC atoms (blockIdx.z
+// selects the atom chunk).  The signal patch of one channel and the matching
+// atom slice are staged in shared memory; thread (r, cg) owns positions
+// (r, cg + q * TPR), q < NQ, so a warp reads consecutive words of the patch
+// while the atom weight is a broadcast.
+template <typename real, int NT, int TR, int NQ, int KC, int EPI>
+__global__ void __launch_bounds__(NT) corr_kernel(CorrArgs<real> a) {
+    constexpr int TPR = NT / TR;
+    constexpr int TC = TPR * NQ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sS = reinterpret_cast<real *>(smem_raw);
+    const int PR = TR + a.L0 - 1, PC = TC + a.L1 - 1;
+    real *sW = sS + (size_t)PR * PC;
+    const int LL = a.L0 * a.L1;
+
+    const int i0 = blockIdx.y * TR, j0 = blockIdx.x * TC, k0 = blockIdx.z * KC;
+    const int r = threadIdx.x / TPR, cg = threadIdx.x % TPR;
+
+    real acc[KC][NQ];
+#pragma unroll
+    for (int kk = 0; kk < KC; kk++)
+#pragma unroll
+        for (int q = 0; q < NQ; q++) acc[kk][q] = real(0);
+
+    for (int p = 0; p < a.P; p++) {
+        __syncthreads();
+        const real *Sp = a.S + (size_t)p * a.T0 * a.T1;
+        for (int e = threadIdx.x; e < PR * PC; e += NT) {
+            int rr = e / PC, cc = e % PC;
+            int gi = i0 + rr, gj = j0 + cc;
+            sS[e] = (gi < a.T0 && gj < a.T1) ? Sp[(size_t)gi * a.T1 + gj] : real(0);
+        }
+        for (int e = threadIdx.x; e < KC * LL; e += NT) {
+            int kk = e / LL, t = e % LL;
+            int k = k0 + kk;
+            sW[e] = k < a.K ? a.Wt[((size_t)k * a.P + p) * LL + t] : real(0);
+        }
+        __syncthreads();
+        for (int ta = 0; ta < a.L0; ta++) {
+            const real *row = sS + (size_t)(r + ta) * PC + cg;
+            const real *wrow = sW + ta * a.L1;
+            for (int tb = 0; tb < a.L1; tb++) {
+                real x[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; q++) x[q] = row[q * TPR + tb];
+#pragma unroll
+                for (int kk = 0; kk < KC; kk++) {
+                    real wv = wrow[kk * LL + tb];
+#pragma unroll
+                    for (int q = 0; q < NQ; q++) acc[kk][q] = fma(wv, x[q], acc[kk][q]);
+                }
+            }
+        }
+    }
+
+    unsigned long long m = 0;
+    const int i = i0 + r;
+#pragma unroll
+    for (int kk = 0; kk < KC; kk++) {
+        int k = k0 + kk;
+        if (k >= a.K || i >= a.Z0) continue;
+        double nk = 0.0;
+        real nr = real(0), inv = real(0);
+        if (EPI == EPI_REFRESH) {
+            nk = a.nrm[k];
+            nr = real(nk);
+            inv = real(1.0 / nk);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            int j = j0 + cg + q * TPR;
+            if (j >= a.Z1) continue;
+            size_t at = ((size_t)k * a.Z0 + i) * a.Z1 + j;
+            real v = acc[kk][q];
+            if (EPI == EPI_INIT) {
+                a.out[at] = v;
+                unsigned long long b = nonneg_bits(v < real(0) ? -v : v);
+                m = b > m ? b : m;
+            } else {
+                real z = a.Zc[at];
+                v = v + nr * z;
+                a.out[at] = v;
+                real dz = coord_update(v, a.lambda, nr, inv) - z;
+                dz = dz < real(0) ? -dz : dz;
+                unsigned long long b = nonneg_bits(dz);
+                m = b > m ? b : m;
+            }
+        }
+    }
+    block_max_atomic<NT>(m, a.bits);
+}
+
+template <typename real, int NT, int TR, int NQ, int KC, int EPI>
+static int run_corr(const Geom &g, CorrArgs<real> a, cudaStream_t st) {
+    constexpr int TC = (NT / TR) * NQ;
+    auto kern = corr_kernel<real, NT, TR, NQ, KC, EPI>;
+    size_t smem = ((size_t)(TR + g.L0 - 1) * (TC + g.L1 - 1) + (size_t)KC * g.L0 * g.L1) * sizeof(real);
+    if (smem > 48 * 1024) {
+        if (smem > 227 * 1024) return CSC_ERR_UNIMPLEMENTED;
+        CSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    dim3 grid((unsigned)ceil_div(g.Z1, TC), (unsigned)ceil_div(g.Z0, TR), (unsigned)ceil_div(g.K, KC));
+    kern<<<grid, NT, smem, st>>>(a);
+    CSC_CUDA(cudaGetLastError());
+    return CSC_OK;
+}
+
+template <typename real, int EPI>
+static int corr_dispatch(const Geom &g, CorrArgs<real> a, cudaStream_t st) {
+    if (g.Z0 == 1) return run_corr<real, 256, 1, 4, 8, EPI>(g, a, st);
+    return run_corr<real, 256, 8, 4, 8, EPI>(g, a, st);
+}
+
+template <typename real>
+int launch_corr_init(const Geom &g, const real *X, const real *D, real *beta,
+                     unsigned long long *lmax_bits, cudaStream_t st) {
+    CorrArgs<real> a{X, D, beta, nullptr, nullptr, real(0), lmax_bits,
+                     g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z0, g.Z1};
+    return corr_dispatch<real, EPI_INIT>(g, a, st);
+}
+
+template <typename real>
+int launch_corr_refresh(const Geom &g, const real *R, const real *D, const real *Z,
+                        const double *nrm, real lambda, real *beta,
+                        unsigned long long *maxdz_bits, cudaStream_t st) {
+    CorrArgs<real> a{R, D, beta, Z, nrm, lambda, maxdz_bits,
+                     g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z0, g.Z1};
+    return corr_dispatch<real, EPI_REFRESH>(g, a, st);
+}
+
+// ------------------------------------------------------------- DtD table
+// One CTA per atom pair (k, k2): both atoms are staged in shared memory and
+// each thread produces table entries delta = (d0, d1).
+template <typename real, int NT>
+__global__ void __launch_bounds__(NT) dtd_kernel(const real *D, real *tab, int P, int K, int L0,
+                                                 int L1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *Da = reinterpret_cast<real *>(smem_raw);
+    const int n = P * L0 * L1;
+    real *Db = Da + n;
+    const int k = blockIdx.y, k2 = blockIdx.x;
+    for (int e = threadIdx.x; e < n; e += NT) {
+        Da[e] = D[(size_t)k * n + e];
+        Db[e] = D[(size_t)k2 * n + e];
+    }
+    __syncthreads();
+    const int W0 = 2 * L0 - 1, W1 = 2 * L1 - 1;
+    for (int w = threadIdx.x; w < W0 * W1; w += NT) {
+        const int d0 = w / W1 - (L0 - 1), d1 = w % W1 - (L1 - 1);
+        const int a_lo = d0 < 0 ? -d0 : 0, a_hi = d0 > 0 ? L0 - d0 : L0;
+        const int b_lo = d1 < 0 ? -d1 : 0, b_hi = d1 > 0 ? L1 - d1 : L1;
+        real acc = real(0);
+        for (int p = 0; p < P; p++)
+            for (int ta = a_lo; ta < a_hi; ta++) {
+                const real *ra = Da + ((size_t)p * L0 + ta) * L1;
+                const real *rb = Db + ((size_t)p * L0 + ta + d0) * L1 + d1;
+                for (int tb = b_lo; tb < b_hi; tb++) acc = fma(ra[tb], rb[tb], acc);
+            }
+        tab[((size_t)k * K + k2) * W0 * W1 + w] = acc;
+    }
+}
+
+template <typename real>
+int launch_dtd(const Geom &g, const real *D, real *dtd, cudaStream_t st) {
+    size_t smem = 2 * (size_t)g.natom() * sizeof(real);
+    auto kern = dtd_kernel<real, 256>;
+    if (smem > 48 * 1024) {
+        if (smem > 227 * 1024) return CSC_ERR_UNIMPLEMENTED;
+        CSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    kern<<<dim3(g.K, g.K), 256, smem, st>>>(D, dtd, g.P, g.K, g.L0, g.L1);
+    CSC_CUDA(cudaGetLastError());
+    return CSC_OK;
+}
+
+// ||D_k||^2 accumulated in FP64 and max_{p,tau} |D_kp[tau]|, one CTA per atom.
+template <typename real, int NT>
+__global__ void __launch_bounds__(NT) atom_norm_kernel(const real *D, int n, double *nrm,
+                                                       double *dmax) {
+    const int k = blockIdx.x;
+    double s = 0.0, m = 0.0;
+    for (int e = threadIdx.x; e < n; e += NT) {
+        double v = (double)D[(size_t)k * n + e];
+        s += v * v;
+        m = fmax(m, fabs(v));
+    }
+    __shared__ double rs[NT / 32], rm[NT / 32];
+    s = warp_sum(s);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) {
+        rs[threadIdx.x >> 5] = s;
+        rm[threadIdx.x >> 5] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ts = 0.0, tm = 0.0;
+        for (int w = 0; w < NT / 32; w++) {
+            ts += rs[w];
+            tm = fmax(tm, rm[w]);
+        }
+        nrm[k] = ts;
+        dmax[k] = tm;
+    }
+}
+
+template <typename real>
+int launch_atom_norms(const Geom &g, const real *D, double *nrm, double *dmax, cudaStream_t st) {
+    atom_norm_kernel<real, 256><<<g.K, 256, 0, st>>>(D, (int)g.natom(), nrm, dmax);
+    CSC_CUDA(cudaGetLastError());
+    return CSC_OK;
+}
+
+#define CSC_INST(real)                                                                         \
+    template int launch_corr_init<real>(const Geom &, const real *, const real *, real *,     \
+                                        unsigned long long *, cudaStream_t);                  \
+    template int launch_corr_refresh<real>(const Geom &, const real *, const real *,          \
+                                           const real *, const double *, real, real *,        \
+                                           unsigned long long *, cudaStream_t);               \
+    template int launch_dtd<real>(const Geom &, const real *, real *, cudaStream_t);          \
+    template int launch_atom_norms<real>(const Geom &, const real *, double *, double *,      \
+                                         cudaStream_t);
+CSC_INST(float)
+CSC_INST(double)
+#undef CSC_INST
+
+}  // namespace csc

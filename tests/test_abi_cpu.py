@@ -1,0 +1,89 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function declared in include/*.h, and rejects
+invalid shapes before touching a device."""
+import ctypes as C
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1901_09235_gb300 import build
+    build.build()
+    import paper_1901_09235_gb300 as pkg
+    return pkg.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names |= set(re.findall(r"CSC_API\s+[\w\s\*]+?\b(\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("csc_init_beta", "csc_lgcd_solve", "cdl_dict_stats", "cdl_dict_update"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1901_09235_gb300 import library_path
+    out = subprocess.run(["nm", "-D", "--defined-only", library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (\w+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert getattr(lib, n) is not None
+
+
+def test_status_strings_and_defaults(lib):
+    import paper_1901_09235_gb300 as pkg
+    assert pkg.status_string(0) == "ok"
+    assert "workspace" in pkg.status_string(7)
+    o = pkg.default_opts()
+    assert o.mode == pkg.MODE_ASYNC and o.beta_refresh == 2 and o.timeout_s > 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(d=3, P=1, K=1, T=(8, 1), L=(2, 1)),
+    dict(d=1, P=0, K=1, T=(8, 1), L=(2, 1)),
+    dict(d=1, P=1, K=1, T=(8, 1), L=(9, 1)),
+    dict(d=1, P=1, K=1, T=(8, 2), L=(2, 1)),
+    dict(d=2, P=1, K=1, T=(8, 8), L=(2, 9)),
+])
+def test_invalid_shapes_rejected_on_host(lib, bad):
+    import paper_1901_09235_gb300 as pkg
+    s = pkg.Shape()
+    s.d, s.P, s.K = bad["d"], bad["P"], bad["K"]
+    s.T[0], s.T[1] = bad["T"]
+    s.L[0], s.L[1] = bad["L"]
+    n = C.c_size_t(0)
+    assert lib.csc_workspace_size(C.byref(s), None, C.byref(n)) == pkg.CSC_ERR_INVALID
+    rc = lib.csc_init_beta(C.byref(s), None, None, None, None, None, None, 0, None)
+    assert rc == pkg.CSC_ERR_INVALID
+
+
+def test_workspace_size_grows_with_problem(lib):
+    import paper_1901_09235_gb300 as pkg
+    a = pkg.workspace_size(pkg.make_shape((1, 64, 64), (5, 1, 8, 8)))
+    b = pkg.workspace_size(pkg.make_shape((1, 256, 256), (5, 1, 8, 8)))
+    assert 0 < a < b
+
+
+def test_null_pointers_rejected(lib):
+    import paper_1901_09235_gb300 as pkg
+    s = pkg.make_shape((2, 100), (3, 2, 5))
+    st = pkg.SolveStats()
+    rc = lib.csc_lgcd_solve(C.byref(s), None, None, None, None, None, 0.1, 1e-4, None, None, 0,
+                            C.byref(st), None)
+    assert rc == pkg.CSC_ERR_INVALID
+    assert lib.cdl_dict_stats(C.byref(s), None, None, None, None, None, 0, None) == pkg.CSC_ERR_INVALID

@@ -1,0 +1,195 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Sizes are small enough for the oracle to finish in seconds yet span several
+CTA tiles / worker tiles with ragged tails."""
+import numpy as np
+import pytest
+
+from synthetic import Workload, make_problem
+from tests._gpu import dev, gamma, host, support_mismatch
+
+pytestmark = pytest.mark.gpu
+
+W_1D = Workload("t1d", P=5, K=10, T=(3001,), L=(64,), density=0.005, sigma=0.1)
+W_2D = Workload("t2d", P=2, K=5, T=(70, 150), L=(8, 12), density=0.01, sigma=0.1)
+W_IMG = Workload("img64", P=1, K=5, T=(64, 64), L=(8, 8), density=0.01, sigma=0.1)
+W_DEG = Workload("deg", P=3, K=1, T=(37, 41), L=(1, 1), density=0.05, sigma=0.1)
+W_ONE = Workload("one", P=2, K=4, T=(9, 7), L=(9, 7), density=1.0, sigma=0.1)
+SHAPES = [W_1D, W_2D, W_IMG, W_DEG, W_ONE]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1901_09235_gb300 as p
+    from paper_1901_09235_gb300 import build
+    build.build()
+    p.load()
+    return p
+
+
+@pytest.mark.parametrize("w", SHAPES, ids=[w.name for w in SHAPES])
+def test_init_beta_and_dtd_fp32(pkg, orc, w):
+    """beta = D~ * X, the D^T D table and lambda_max within the gamma_n bound
+    of an n = P|Theta| term fp32 dot product."""
+    import torch
+    X, D, _ = make_problem(w, 21)
+    beta, dtd, lmax = pkg.csc_init_beta(dev(X), dev(D))
+    torch.cuda.synchronize()
+    ref = orc.beta_init(X, D)
+    n = w.P * int(np.prod(w.L))
+    bound = gamma(n) * orc.beta_init(np.abs(X), np.abs(D)) + 1e-30
+    assert np.all(np.abs(host(beta) - ref) <= bound)
+    d = len(w.L)
+    tref = orc.dtd(D, d)
+    tbound = gamma(n) * orc.dtd(np.abs(D), d) + 1e-30
+    assert np.all(np.abs(host(dtd) - tref) <= tbound)
+    assert abs(lmax - np.abs(ref).max()) <= bound.max()
+
+
+@pytest.mark.parametrize("w", [W_1D, W_2D], ids=["1d", "2d"])
+def test_init_beta_fp64(pkg, orc, w):
+    import torch
+    X, D, _ = make_problem(w, 22)
+    beta, dtd, lmax = pkg.csc_init_beta(dev(X, torch.float64), dev(D, torch.float64))
+    n = w.P * int(np.prod(w.L))
+    bound = gamma(n, 2.0 ** -53) * orc.beta_init(np.abs(X), np.abs(D)) * 2 + 1e-300
+    assert np.all(np.abs(host(beta) - orc.beta_init(X, D)) <= bound)
+    assert abs(lmax - orc.lambda_max(X, D)) <= bound.max()
+
+
+PHASED = [
+    (Workload("p1d", P=2, K=3, T=(600,), L=(16,), density=0.01, sigma=0.1), (64,)),
+    (Workload("p1d_b", P=1, K=2, T=(500,), L=(9,), density=0.02, sigma=0.1), (40,)),
+    (Workload("p2d", P=1, K=3, T=(60, 70), L=(6, 5), density=0.01, sigma=0.1), (14, 12)),
+    (Workload("p2d_b", P=2, K=2, T=(45, 33), L=(4, 4), density=0.02, sigma=0.1), (8, 9)),
+]
+
+
+@pytest.mark.parametrize("w,tile", PHASED, ids=[p[0].name for p in PHASED])
+def test_phased_fp64_equals_oracle_schedule(pkg, orc, w, tile):
+    """The deterministic checkerboard mode in FP64 makes the same choices as
+    the oracle's tiled schedule: same number of updates, same Z to 1e-12."""
+    import torch
+    X, D, _ = make_problem(w, 23)
+    lam = 0.1 * orc.lambda_max(X, D)
+    tol = 1e-6
+    ref = orc.lgcd(X, D, lam, tol, tile=tile)
+    assert ref["status"] == 0
+    Xd, Dd = dev(X, torch.float64), dev(D, torch.float64)
+    beta, dtd, _ = pkg.csc_init_beta(Xd, Dd)
+    opts = pkg.default_opts(mode=pkg.MODE_PHASED, tile=tile, beta_refresh=0)
+    Z, st = pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, lam, tol, opts=opts)
+    assert st["status"] == 0, st
+    assert st["updates"] == ref["n_updates"]
+    np.testing.assert_allclose(host(Z), ref["Z"], rtol=0, atol=1e-12)
+    assert st["max_dz_final"] < tol
+
+
+@pytest.mark.parametrize("w,tile", PHASED, ids=[p[0].name for p in PHASED])
+def test_phased_fp32_objective(pkg, orc, w, tile):
+    X, D, _ = make_problem(w, 24)
+    lam = 0.1 * orc.lambda_max(X, D)
+    tol = 1e-4
+    ref = orc.lgcd(X, D, lam, tol, tile=tile)
+    Xd, Dd = dev(X), dev(D)
+    beta, dtd, _ = pkg.csc_init_beta(Xd, Dd)
+    opts = pkg.default_opts(mode=pkg.MODE_PHASED, tile=tile)
+    Z, st = pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, lam, tol, opts=opts)
+    assert st["status"] == 0, st
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    f_gpu = orc.objective(X, D, host(Z), lam)
+    assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
+    assert orc.kkt(X, D, host(Z), lam) < 1.05 * tol
+
+
+ASYNC = [
+    Workload("a1d", P=5, K=10, T=(20000,), L=(64,), density=0.005, sigma=0.1),
+    Workload("a1d_small_tiles", P=2, K=4, T=(5000,), L=(16,), density=0.01, sigma=0.1),
+    W_IMG,
+    Workload("a2d", P=1, K=5, T=(200, 230), L=(8, 8), density=0.01, sigma=0.1),
+    Workload("a2d_rgb", P=3, K=6, T=(120, 90), L=(12, 12), density=0.002, sigma=0.1),
+]
+
+
+@pytest.mark.parametrize("w", ASYNC, ids=[w.name for w in ASYNC])
+def test_async_softlock_matches_oracle(pkg, orc, w):
+    """Asynchronous tiles with soft-locks reach the oracle's objective within
+    1e-5 relative, satisfy max|dZ| < tol on a beta recomputed in FP64, and
+    differ from the oracle's support only on small coordinates."""
+    X, D, _ = make_problem(w, 25)
+    lam = 0.1 * orc.lambda_max(X, D)
+    tol = 1e-4
+    ref = orc.lgcd(X, D, lam, tol)
+    Xd, Dd = dev(X), dev(D)
+    beta, dtd, _ = pkg.csc_init_beta(Xd, Dd)
+    Z, st = pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, lam, tol)
+    assert st["status"] == 0, st
+    assert st["workers"] > 1
+    Zh = host(Z)
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    f_gpu = orc.objective(X, D, Zh, lam)
+    assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
+    assert abs(st["objective"] - f_gpu) <= 1e-6 * abs(f_gpu)
+    assert orc.kkt(X, D, Zh, lam) < 1.05 * tol
+    nnz = int((ref["Z"] != 0).sum())
+    cnt, worst = support_mismatch(Zh, ref["Z"], tol)
+    assert cnt <= max(10, 0.01 * nnz), (cnt, nnz)
+    assert worst <= 100 * tol
+
+
+def test_lambda_max_gives_zero(pkg, orc):
+    """lambda >= lambda_max: Z = 0 exactly and no update (Section 2)."""
+    X, D, _ = make_problem(W_2D, 26)
+    Xd, Dd = dev(X), dev(D)
+    beta, dtd, lmax = pkg.csc_init_beta(Xd, Dd)
+    Z, st = pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, lmax * 1.0001, 1e-4)
+    assert st["status"] == 0 and st["updates"] == 0
+    assert not host(Z).any()
+
+
+def test_objective_call(pkg, orc):
+    rng = np.random.default_rng(0)
+    X, D, Z = make_problem(W_2D, 27)
+    Zp = (Z + 0.01 * rng.standard_normal(Z.shape) * (rng.random(Z.shape) < 0.01)).astype(np.float32)
+    lam = 0.37
+    got = pkg.csc_objective(dev(X), dev(D), dev(Zp), lam)
+    ref = orc.objective(X, D, Zp, lam)
+    assert abs(got - ref) <= 1e-12 * abs(ref) + 1e-12
+
+
+@pytest.mark.parametrize("w", [W_1D, W_2D, W_IMG], ids=["1d", "2d", "img"])
+def test_dict_stats(pkg, orc, w):
+    """phi and psi from the nonzeros of Z (Section 4.2) against their
+    definitions; psi partial sums run in fp32 over chunks of 64 nonzeros."""
+    X, D, Z = make_problem(w, 28)
+    phi, psi = pkg.cdl_dict_stats(dev(Z), dev(X), D.shape)
+    pref, sref = orc.phi_psi(Z, X, w.L)
+    np.testing.assert_allclose(host(phi), pref, rtol=1e-6, atol=1e-6 * np.abs(pref).max())
+    sb = gamma(64) * orc.phi_psi(np.abs(Z), np.abs(X), w.L)[1] * 2 + 1e-7 * np.abs(sref).max()
+    assert np.all(np.abs(host(psi) - sref) <= sb)
+
+
+@pytest.mark.parametrize("w", [W_1D, W_2D, W_IMG], ids=["1d", "2d", "img"])
+def test_dict_update(pkg, orc, w):
+    """PGD + Armijo on the same (phi, psi): the GPU objective matches the
+    oracle's, every atom stays in the unit ball, and F does not increase."""
+    import torch
+    X, D, Z = make_problem(w, 29)
+    rng = np.random.default_rng(3)
+    D0 = (D + 0.3 * rng.standard_normal(D.shape)).astype(np.float32)
+    phi, psi = orc.phi_psi(Z, X, w.L)
+    phi32, psi32 = phi.astype(np.float32), psi.astype(np.float32)
+    xs = float(np.sum(X.astype(np.float64) ** 2))
+    Dd = dev(D0)
+    f_gpu, it = pkg.cdl_dict_update(dev(phi32), dev(psi32), xs, Dd, X.shape, max_iter=50, tol=1e-8)
+    D_ref, f_ref, it_ref = orc.pgd_armijo(phi32, psi32, xs, D0, max_iter=50, tol=1e-8)
+    f0 = orc.dict_objective(phi32, psi32, xs, D0)
+    Dg = host(Dd)
+    assert f_gpu <= f0
+    assert abs(orc.dict_objective(phi32, psi32, xs, Dg) - f_gpu) <= 1e-6 * abs(f0)
+    assert abs(f_gpu - f_ref) <= 1e-5 * abs(f0 - f_ref) + 1e-7 * abs(f_ref)
+    nr = np.sqrt((Dg.reshape(w.K, -1).astype(np.float64) ** 2).sum(1))
+    assert np.all(nr <= 1 + 1e-6)
