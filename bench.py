@@ -1,0 +1,373 @@
+"""Benchmark of the CSC hot path on GB300.
+
+One step = one pass of the whole path over one synthetic problem of the 1-D
+multichannel workload (P = 5, T = 200,000, K = 10 atoms of L = 64):
+  csc_init_beta (beta = D~ * X, the D^T D table, lambda_max)
+  csc_lgcd_solve (LGCD with soft-locks to max |dZ| < 1e-4, lambda = 0.1 lambda_max,
+                  FP64 objective and KKT on a beta recomputed from scratch)
+  cdl_dict_stats (phi, psi) and cdl_dict_update (PGD + Armijo on D).
+Every step starts from the same X and initial D.  The metric is solves/s
+(one solve per step) with p50/p99 step latency and coordinate updates/s.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+launching stream; L2 is flushed (256 MiB write) between steps outside the
+events.  `e2e` repeats the measurement through host buffers (pinned X and D
+copied in, D and the objective copied out every step).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+Under torchrun (N > 1) every rank solves its own problem (independent
+replicas, no collective on the data path); value = all solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CSC coordinate updates/s and solves/s to tol 1e-4 (p50/p99 latency), 1 GB300 vs plain"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    from synthetic import SIGNAL_200K
+    return SIGNAL_200K
+
+
+def config_dict(w, extra=None):
+    d = {"workload": w.name, "P": w.P, "K": w.K, "T": list(w.T), "L": list(w.L),
+         "density": w.density, "sigma": w.sigma, "lambda": f"{w.reg} * lambda_max", "tol": w.tol,
+         "step": "init_beta + lgcd_solve + dict_stats + dict_update",
+         "l2": "flushed between steps (256 MiB write), inputs 4 MB < L2"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- GPU arm
+class GpuStep:
+    """Device-resident buffers and one hot-path step through the C ABI."""
+
+    def __init__(self, X, D0, w, device):
+        import torch
+        import paper_1901_09235_gb300 as pkg
+        self.pkg, self.w = pkg, w
+        self.X = torch.from_numpy(X).to(device)
+        self.D0 = torch.from_numpy(D0).to(device)
+        self.D = self.D0.clone()
+        self.prob = pkg.Problem.create(self.X, self.D)
+        self.xs = float((X.astype(np.float64) ** 2).sum())
+        self.opts = pkg.default_opts()
+        self.last = {}
+
+    def run(self, X=None, D=None):
+        pkg, p = self.pkg, self.prob
+        Xd = self.X if X is None else X
+        if D is None:
+            self.D.copy_(self.D0, non_blocking=True)
+            D = self.D
+        _, _, lmax = pkg.csc_init_beta(Xd, D, p.beta, p.dtd, p.ws)
+        lam = self.w.reg * lmax
+        Z, st = pkg.csc_lgcd_solve(Xd, D, p.dtd, p.beta, lam, self.w.tol, Z=p.Z, opts=self.opts,
+                                   ws=p.ws)
+        if st["status"] != pkg.CSC_OK:
+            raise RuntimeError(f"solve status {st['status']}: {pkg.status_string(st['status'])}")
+        pkg.cdl_dict_stats(Z, Xd, tuple(D.shape), p.phi, p.psi, p.ws)
+        F, it = pkg.cdl_dict_update(p.phi, p.psi, self.xs, D, tuple(Xd.shape), max_iter=50, tol=1e-8,
+                                    ws=p.ws)
+        st["dict_F"], st["dict_iters"], st["lambda"] = F, it, lam
+        self.last = st
+        return st
+
+
+def launches_per_step(st):
+    # init_beta: corr + dtd; solve: atom norms + per round (header reset, LGCD,
+    # 8 refresh kernels); dict_stats: 7; dict_update: 1
+    return 2 + 1 + 10 * int(st["refresh_rounds"]) + 7 + 1
+
+
+def lgcd_algorithmic_bytes(st, w):
+    """Bytes one LGCD launch must move by its definition: every iteration
+    reads beta and Z over K x |C_m| (8 B per candidate); every accepted update
+    reads and writes beta and reads the D^T D table over K x |window|
+    (12 B per entry) and writes one Z (4 B)."""
+    K = w.K
+    sub = int(np.prod([2 * l for l in w.L]))
+    win = int(np.prod([2 * l - 1 for l in w.L]))
+    return st["iterations"] * 8 * K * sub + st["updates"] * (12 * K * win + 4)
+
+
+def smem_peak_gbs(sm_mhz=2070.0, sms=152):
+    """Shared-memory bandwidth: 128 B per clock per SM (32 banks x 4 B)."""
+    return sms * 128 * sm_mhz * 1e6 / 1e9
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def time_gpu(step, steps, warmup, flush, stream, e2e=None):
+    import torch
+    for _ in range(warmup):
+        step.run() if e2e is None else e2e()
+    torch.cuda.synchronize()
+    times, stats = [], []
+    for _ in range(steps):
+        flush_l2(flush)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record(stream)
+        st = step.run() if e2e is None else e2e()
+        e.record(stream)
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e) / 1e3)
+        stats.append(dict(st))
+    return times, stats
+
+
+def cpu_oracle_step(X, D0, w):
+    import oracle
+    t0 = time.perf_counter()
+    lm = oracle.lambda_max(X, D0)
+    lam = w.reg * lm
+    out = oracle.lgcd(X, D0, lam, w.tol)
+    Z = out["Z"]
+    oracle.objective(X, D0, Z, lam)
+    phi, psi = oracle.phi_psi(Z, X, w.L)
+    xs = float((X.astype(np.float64) ** 2).sum())
+    oracle.pgd_armijo(phi, psi, xs, D0, max_iter=50, tol=1e-8)
+    return time.perf_counter() - t0, out["n_updates"]
+
+
+def cpu_baseline(X, D0, w, seconds):
+    import oracle
+    oracle.build()
+    done, total, upd = 0, 0.0, 0
+    while total < seconds and done < 20:
+        dt, u = cpu_oracle_step(X, D0, w)
+        total += dt
+        upd += u
+        done += 1
+    return {"value": done / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} full oracle steps of the same workload (lambda_max, LGCD, objective, "
+                      f"phi/psi, PGD) on one core, {total:.1f} s",
+            "updates_per_s": upd / total}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    w = workload()
+    from synthetic import make_problem
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        X, D0, _ = make_problem(w, args.seed)
+        import oracle
+        oracle.build()
+        for _ in range(args.warmup):
+            cpu_oracle_step(X, D0, w)
+        times = []
+        upd = 0
+        for _ in range(args.steps):
+            dt, u = cpu_oracle_step(X, D0, w)
+            times.append(dt)
+            upd += u
+        total = sum(times)
+        val = args.steps / total
+        line = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": config_dict(w, {"arm": "FP64 CPU oracle, single thread"}),
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{args.steps} full oracle steps"},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "updates_per_s": upd / total,
+                "p50_ms": 1e3 * float(np.percentile(times, 50)),
+                "p99_ms": 1e3 * float(np.percentile(times, 99))}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    X, D0, _ = make_problem(w, args.seed + rank)
+    step = GpuStep(X, D0, w, device)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        times, stats = time_gpu(step, args.steps, max(3, args.warmup), flush, stream)
+    barrier()
+    clocks = clk.summary()
+
+    # end to end through host buffers: pinned X / D in, D and objective out
+    Xh = torch.from_numpy(X).pin_memory()
+    Dh = torch.from_numpy(D0).pin_memory()
+    Dout = torch.empty_like(Dh).pin_memory()
+    Xe = torch.empty_like(step.X)
+    De = torch.empty_like(step.D)
+
+    def e2e_step():
+        Xe.copy_(Xh, non_blocking=True)
+        De.copy_(Dh, non_blocking=True)
+        st = step.run(Xe, De)
+        Dout.copy_(De, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return st
+
+    e2e_times, _ = time_gpu(step, args.steps, max(3, args.warmup), flush, stream, e2e=e2e_step)
+    barrier()
+
+    tot = sum(times)
+    tot_e2e = sum(e2e_times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot, tot_e2e], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot, tot_e2e = float(t[0]), float(t[1])
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+
+    upd = sum(s["updates"] for s in stats)
+    kms = [s["kernel_ms"] for s in stats]
+    kernel_s = sum(kms) / 1e3
+    abytes = sum(lgcd_algorithmic_bytes(s, w) for s in stats)
+    achieved = abytes / kernel_s / 1e9
+    peak = smem_peak_gbs()
+    last = stats[-1]
+    line = {
+        "metric": METRIC, "value": world * args.steps / tot, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": config_dict(w, {"parallelism": f"replicas{world}" if world > 1 else "single",
+                                  "workers": last["workers"], "tile": last["tile_size"][0]}),
+        "updates_per_s": world * upd / tot,
+        "p50_ms": 1e3 * float(np.percentile(times, 50)),
+        "p99_ms": 1e3 * float(np.percentile(times, 99)),
+        "lgcd_kernel_ms_per_step": 1e3 * kernel_s / args.steps,
+        "lgcd_updates_per_s_kernel": upd / kernel_s,
+        "objective": last["objective"], "max_dz_final": last["max_dz_final"], "nnz": last["nnz"],
+        "updates_per_solve": upd / args.steps,
+        "solve_stats": {k: last[k] for k in ("iterations", "rejected_softlock", "skipped_subtol",
+                                              "messages", "deferred", "refresh_rounds",
+                                              "max_worker_iterations", "max_worker_updates",
+                                              "kernel_ms", "dict_iters")},
+        "roofline": {"bound": "smem", "kernel": "lgcd_async_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 B/clk x 2070 MHz (shared memory)",
+                     "algorithmic_bytes_per_launch": abytes / len(stats)},
+        "e2e": {"value": world * args.steps / tot_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(Xh.numel() * 4 + Dh.numel() * 4),
+                "d2h_bytes_per_step": int(Dout.numel() * 4 + 8)},
+        "gpu_launches": sum(launches_per_step(s) for s in stats),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(X, D0, w, args.cpu_seconds)
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

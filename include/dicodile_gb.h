@@ -99,6 +99,9 @@ typedef struct {
     double objective;            /* 1/2||X - Z*D||^2 + lambda||Z||_1, FP64 accumulation   */
     long long nnz;               /* nonzeros of Z at the end                             */
     double kernel_ms;            /* device time of the LGCD launches (CUDA events)       */
+    long long deferred;          /* accepted candidates postponed: a neighbour inbox was full */
+    long long max_worker_iterations; /* iterations of the busiest worker (critical path)  */
+    long long max_worker_updates;    /* updates of the busiest worker                      */
     int status;                  /* the returned status                                  */
 } csc_solve_stats;
 

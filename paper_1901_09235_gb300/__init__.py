@@ -42,7 +42,9 @@ class SolveStats(C.Structure):
                 ("messages", C.c_longlong), ("refresh_rounds", C.c_longlong),
                 ("workers", C.c_int), ("tiles", C.c_int * 2), ("tile_size", C.c_int * 2),
                 ("max_dz_final", C.c_double), ("objective", C.c_double),
-                ("nnz", C.c_longlong), ("kernel_ms", C.c_double), ("status", C.c_int)]
+                ("nnz", C.c_longlong), ("kernel_ms", C.c_double), ("deferred", C.c_longlong),
+                ("max_worker_iterations", C.c_longlong), ("max_worker_updates", C.c_longlong),
+                ("status", C.c_int)]
 
     def as_dict(self):
         out = {}

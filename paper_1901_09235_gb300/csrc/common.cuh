@@ -48,6 +48,7 @@ struct alignas(128) WsHeader {
     unsigned long long updates_total;  // global update count (max_updates check)
     int pad5[30];
     long long stat[8];      // updates, iterations, rejected, subtol, messages, deferred
+    unsigned long long wmax[2];        // largest per-worker iteration / update counts
     unsigned long long lmax_bits;      // max |beta| (as bits of a non-negative float/double)
     unsigned long long maxdz_bits;     // max |dZ| on a fresh beta
     long long nnz;          // compacted nonzeros of Z (may exceed the capacity)

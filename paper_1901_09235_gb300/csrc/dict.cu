@@ -20,6 +20,9 @@
 // cancellation of subtracting two nearly equal objective values in FP32.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -222,73 +225,97 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
 }
 
 // ====================================================== PGD + Armijo step
+// Cluster layout: CTA r owns whole atoms [r ka, (r+1) ka), so the
+// projection norms are local.  Its slices of D, the gradient G, the trial
+// point and phi * (trial - D) live in shared memory; the trial difference is
+// published (double-buffered) for the other CTAs, which gather the full
+// difference through distributed shared memory before the convolution.
+// Scalars are combined by publishing per-CTA partials and reading them from
+// every rank after one cluster barrier (double-buffered as well), so one
+// Armijo trial costs two cluster barriers.
 struct PgdArgs {
     const float *phi, *psi;
     float *D;      // in/out
-    float *G;      // gradient phi * D - psi
-    float *Dn;     // trial point
-    float *Del;    // D+ - D (read by every CTA)
-    float *Q;      // phi * (D+ - D)
     double *out;   // [objective, iterations, eta]
     double x_sqnorm, tol;
-    int K, P, L0, L1, max_iter;
+    int K, P, L0, L1, max_iter, ka, stage_phi;
 };
 
 constexpr int kPgdThreads = 1024;
-constexpr int kPgdMaxK = 64;
+constexpr int kPgdWarps = kPgdThreads / 32;
 
-// Sum over the cluster of per-CTA partial vectors of length n (n <= 64).
-__device__ __forceinline__ void cluster_sum(cg::cluster_group &cl, double *part, double *tot, int n) {
-    cl.sync();
-    if (threadIdx.x < n) {
-        double s = 0.0;
-        for (unsigned r = 0; r < cl.num_blocks(); r++) s += cl.map_shared_rank(part, r)[threadIdx.x];
-        tot[threadIdx.x] = s;
-    }
-    cl.sync();
-}
+struct PgdSmem {
+    float *del;       // full trial difference, K * per (gathered)
+    float *pubdel[2]; // own trial difference, ka * per, double-buffered
+    float *d, *g, *dn, *q;
+    float *phi;       // own rows of phi (optional)
+};
 
-// Block-wide sums of up to 4 values into part[0..3] (thread 0 writes).
-__device__ __forceinline__ void block_sums4(double v0, double v1, double v2, double v3, double *part) {
-    __shared__ double red[4][kPgdThreads / 32];
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    v2 = warp_sum(v2);
-    v3 = warp_sum(v3);
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = v0;
-        red[1][threadIdx.x >> 5] = v1;
-        red[2][threadIdx.x >> 5] = v2;
-        red[3][threadIdx.x >> 5] = v3;
+// Block-wide sum returned to every thread (warp 0 combines the warp sums).
+__device__ __forceinline__ double block_reduce_sum(double v, double *scratch) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = warp_sum(scratch[threadIdx.x]);
+        if (threadIdx.x == 0) scratch[kPgdWarps] = s;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int w = 0; w < kPgdThreads / 32; w++) s += red[threadIdx.x][w];
-        part[threadIdx.x] = s;
-    }
-    __syncthreads();
+    return scratch[kPgdWarps];
 }
 
-// out[e] = sum_k2 sum_tau2 phi_{k,k2}[tau - tau2] src[k2][p][tau2] over this
-// CTA's slice of entries e = (k, p, tau); src is staged in shared memory.
-__device__ __forceinline__ void phi_conv_slice(const PgdArgs &a, const float *ssrc, float *out, int lo,
-                                               int hi) {
+// q[e] = sum_k2 sum_tau2 phi_{k,k2}[tau - tau2] src[k2][p][tau2] for the own
+// entries e = (k, p, ta, tb).  A task is (own row (k, p, ta), four
+// consecutive tb, one source atom k2): it slides a four-wide window of the
+// phi row along tau2 so every step is one broadcast load of src, one load
+// of phi and four FMAs; the K partial sums of an output are combined with
+// shared-memory atomics.
+__device__ __forceinline__ void phi_conv_own(const PgdArgs &a, const PgdSmem &S, int k_lo, int nown,
+                                             const float *src, float *q) {
     const int LL = a.L0 * a.L1, per = a.P * LL;
-    const int W0 = 2 * a.L0 - 1, W1 = 2 * a.L1 - 1;
-    for (int e = lo + threadIdx.x; e < hi; e += kPgdThreads) {
-        const int k = e / per, r = e % per, p = r / LL, t = r % LL, ta = t / a.L1, tb = t % a.L1;
-        float acc = 0.f;
-        for (int k2 = 0; k2 < a.K; k2++) {
-            const float *ph = a.phi + (size_t)(k * a.K + k2) * W0 * W1;
-            const float *sv = ssrc + (size_t)k2 * per + p * LL;
-            for (int a2 = 0; a2 < a.L0; a2++) {
-                const float *prow = ph + (ta - a2 + a.L0 - 1) * W1 + tb + a.L1 - 1;
-                const float *srow = sv + a2 * a.L1;
-                for (int b2 = 0; b2 < a.L1; b2++) acc = fmaf(__ldg(prow - b2), srow[b2], acc);
+    const int W0 = 2 * a.L0 - 1, W1 = 2 * a.L1 - 1, WW = W0 * W1;
+    for (int e = threadIdx.x; e < nown; e += kPgdThreads) q[e] = 0.f;
+    __syncthreads();
+    const int nb = (a.L1 + 3) / 4;                 // tb blocks per row
+    const int rows = nown / a.L1;                  // own rows (k, p, ta)
+    const int ntask = rows * nb * a.K;
+    for (int task = threadIdx.x; task < ntask; task += kPgdThreads) {
+        const int k2 = task % a.K;
+        const int rb = task / a.K;
+        const int row = rb / nb, tb0 = (rb % nb) * 4;
+        const int kl = row / (a.P * a.L0), rem = row % (a.P * a.L0), p = rem / a.L0, ta = rem % a.L0;
+        const float *ph = (a.stage_phi ? S.phi + (size_t)kl * a.K * WW
+                                       : a.phi + (size_t)(k_lo + kl) * a.K * WW) + (size_t)k2 * WW;
+        const float *sv = src + (size_t)k2 * per + p * LL;
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        for (int a2 = 0; a2 < a.L0; a2++) {
+            // phi index along the row: tb - b2 + L1 - 1, for tb = tb0 .. tb0 + 3
+            const float *prow = ph + (ta - a2 + a.L0 - 1) * W1 + tb0 + a.L1 - 1;
+            const float *srow = sv + a2 * a.L1;
+            // f_q holds phi at row index tb0 + q - b2 + L1 - 1; outputs past the
+            // row end (ragged last block) start at zero and are discarded
+            float f0 = prow[0];
+            float f1 = tb0 + 1 < a.L1 ? prow[1] : 0.f;
+            float f2 = tb0 + 2 < a.L1 ? prow[2] : 0.f;
+            float f3 = tb0 + 3 < a.L1 ? prow[3] : 0.f;
+            for (int b2 = 0; b2 < a.L1; b2++) {
+                const float x = srow[b2];
+                acc0 = fmaf(f0, x, acc0);
+                acc1 = fmaf(f1, x, acc1);
+                acc2 = fmaf(f2, x, acc2);
+                acc3 = fmaf(f3, x, acc3);
+                f3 = f2;
+                f2 = f1;
+                f1 = f0;
+                f0 = (b2 + 1 < a.L1) ? prow[-(b2 + 1)] : 0.f;
             }
         }
-        out[e] = acc;
+        float *qo = q + (size_t)row * a.L1 + tb0;
+        atomicAdd(qo, acc0);
+        if (tb0 + 1 < a.L1) atomicAdd(qo + 1, acc1);
+        if (tb0 + 2 < a.L1) atomicAdd(qo + 2, acc2);
+        if (tb0 + 3 < a.L1) atomicAdd(qo + 3, acc3);
     }
 }
 
@@ -296,82 +323,146 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LL = a.L0 * a.L1, per = a.P * LL, n = a.K * per;
-    float *ssrc = reinterpret_cast<float *>(smem_raw);  // full D or Delta
-    __shared__ double part[kPgdMaxK + 8], tot[kPgdMaxK + 8];
-    __shared__ double sc[4];
+    const int W0 = 2 * a.L0 - 1, W1 = 2 * a.L1 - 1, WW = W0 * W1;
     const int rank = (int)cl.block_rank(), ncl = (int)cl.num_blocks();
-    const int chunk = (n + ncl - 1) / ncl;
-    const int lo = min(n, rank * chunk), hi = min(n, lo + chunk);
-    const int W0 = 2 * a.L0 - 1, W1 = 2 * a.L1 - 1;
+    const int k_lo = min(a.K, rank * a.ka), k_hi = min(a.K, k_lo + a.ka);
+    const int nk = k_hi - k_lo, nown = nk * per, e0 = k_lo * per;
+    const int own_cap = a.ka * per;
 
-    // Lipschitz bound: max_k sum_k2 sum_d |phi_{k,k2}[d]| (rows split over CTAs).
-    {
-        const long long row = (long long)a.K * W0 * W1;
-        for (int k = 0; k < a.K; k++) {
-            double s = 0.0;
-            long long rlo = row * rank / ncl, rhi = row * (rank + 1) / ncl;
-            for (long long q = rlo + threadIdx.x; q < rhi; q += kPgdThreads)
-                s += fabs((double)a.phi[(size_t)k * row + q]);
-            block_sums4(s, 0, 0, 0, sc);
-            if (threadIdx.x == 0) part[k] = sc[0];
+    PgdSmem S;
+    float *f = reinterpret_cast<float *>(smem_raw);
+    S.del = f;
+    f += n;
+    S.pubdel[0] = f;
+    f += own_cap;
+    S.pubdel[1] = f;
+    f += own_cap;
+    S.d = f;
+    f += own_cap;
+    S.g = f;
+    f += own_cap;
+    S.dn = f;
+    f += own_cap;
+    S.q = f;
+    f += own_cap;
+    S.phi = f;
+
+    __shared__ double pub[2][8];
+    __shared__ double scratch[kPgdWarps + 1];
+    __shared__ double anrm[16];
+    __shared__ double bcast[4];
+    int pb = 0;
+    // publish up to 4 block totals, one cluster barrier, read the cluster sums
+    auto cluster_sum4 = [&](double v0, double v1, double v2, double v3, double *out4, bool as_max0) {
+        if (threadIdx.x == 0) {
+            pub[pb][0] = v0;
+            pub[pb][1] = v1;
+            pub[pb][2] = v2;
+            pub[pb][3] = v3;
         }
-        cluster_sum(cl, part, tot, a.K);
-    }
-    double lip = 0.0;
-    for (int k = 0; k < a.K; k++) lip = fmax(lip, tot[k]);
+        cl.sync();
+        if (threadIdx.x < 32) {
+            double t[4] = {0, 0, 0, 0};
+            if ((int)threadIdx.x < ncl) {
+                const double *rp = cl.map_shared_rank(&pub[pb][0], (unsigned)threadIdx.x);
+                for (int i = 0; i < 4; i++) t[i] = rp[i];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                double x = __shfl_xor_sync(0xffffffffu, t[0], o);
+                t[0] = as_max0 ? fmax(t[0], x) : t[0] + x;
+                for (int i = 1; i < 4; i++) t[i] += __shfl_xor_sync(0xffffffffu, t[i], o);
+            }
+            if (threadIdx.x == 0)
+                for (int i = 0; i < 4; i++) bcast[i] = t[i];
+        }
+        __syncthreads();
+        for (int i = 0; i < 4; i++) out4[i] = bcast[i];
+        pb ^= 1;
+    };
 
-    // G = phi * D - psi
-    for (int e = threadIdx.x; e < n; e += kPgdThreads) ssrc[e] = a.D[e];
+    // stage own slices, own rows of phi, the full D (for the first gradient)
+    for (int e = threadIdx.x; e < nown; e += kPgdThreads) S.d[e] = a.D[e0 + e];
+    for (int e = threadIdx.x; e < n; e += kPgdThreads) S.del[e] = a.D[e];
+    if (a.stage_phi)
+        for (size_t e = threadIdx.x; e < (size_t)nk * a.K * WW; e += kPgdThreads)
+            S.phi[e] = a.phi[(size_t)k_lo * a.K * WW + e];
     __syncthreads();
-    phi_conv_slice(a, ssrc, a.G, lo, hi);
-    for (int e = lo + threadIdx.x; e < hi; e += kPgdThreads) a.G[e] -= a.psi[e];
+
+    // Lipschitz bound max_k sum_k2 sum_d |phi_{k,k2}[d]| over own rows, then cluster max
+    double lip_loc = 0.0;
+    for (int kl = 0; kl < nk; kl++) {
+        double s = 0.0;
+        for (size_t q = threadIdx.x; q < (size_t)a.K * WW; q += kPgdThreads)
+            s += fabs((double)a.phi[(size_t)(k_lo + kl) * a.K * WW + q]);
+        lip_loc = fmax(lip_loc, block_reduce_sum(s, scratch));
+    }
+    // G = phi * D - psi on the own slice
+    phi_conv_own(a, S, k_lo, nown, S.del, S.q);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nown; e += kPgdThreads) S.g[e] = S.q[e] - a.psi[e0 + e];
+    double tot[4];
+    cluster_sum4(lip_loc, 0, 0, 0, tot, true);
+    const double lip = tot[0];
 
     double eta = lip > 0.0 ? 1.0 / lip : 0.0;
-    int it = 0;
+    int it = 0, tb = 0;
     if (lip > 0.0) {
         for (it = 0; it < a.max_iter; it++) {
             if (it > 0) eta *= 2.0;
             double dsq = 0.0, dnorm = 0.0;
             for (int bt = 0; bt < 60; bt++) {
-                // trial point and per-atom squared norms
-                for (int k = threadIdx.x; k < a.K; k += kPgdThreads) part[k] = 0.0;
+                // trial point, projected atom by atom (norms are local)
                 __syncthreads();
-                for (int e = lo + threadIdx.x; e < hi; e += kPgdThreads) {
-                    float v = a.D[e] - (float)eta * a.G[e];
-                    a.Dn[e] = v;
-                    atomicAdd(&part[e / per], (double)v * (double)v);
+                for (int e = threadIdx.x; e < nown; e += kPgdThreads) S.dn[e] = S.d[e] - (float)eta * S.g[e];
+                __syncthreads();
+                for (int kl = 0; kl < nk; kl++) {
+                    double s = 0.0;
+                    for (int e = threadIdx.x; e < per; e += kPgdThreads) {
+                        double v = S.dn[kl * per + e];
+                        s += v * v;
+                    }
+                    s = block_reduce_sum(s, scratch);
+                    if (threadIdx.x == 0) anrm[kl] = sqrt(s);
                 }
-                cluster_sum(cl, part, tot, a.K);
+                __syncthreads();
                 double dd = 0.0, d0 = 0.0;
-                for (int e = lo + threadIdx.x; e < hi; e += kPgdThreads) {
-                    double nr = sqrt(tot[e / per]);
-                    float v = a.Dn[e];
+                float *pd = S.pubdel[tb];
+                for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
+                    double nr = anrm[e / per];
+                    float v = S.dn[e];
                     if (nr > 1.0) v = (float)((double)v / nr);
-                    a.Dn[e] = v;
-                    float dl = v - a.D[e];
-                    a.Del[e] = dl;
+                    S.dn[e] = v;
+                    float dl = v - S.d[e];
+                    pd[e] = dl;
                     dd += (double)dl * dl;
-                    d0 += (double)a.D[e] * a.D[e];
+                    d0 += (double)S.d[e] * S.d[e];
                 }
-                cl.sync();  // Delta complete in global memory
-                for (int e = threadIdx.x; e < n; e += kPgdThreads) ssrc[e] = __ldcg(a.Del + e);
-                __syncthreads();
-                phi_conv_slice(a, ssrc, a.Q, lo, hi);
-                double qd = 0.0;
-                for (int e = lo + threadIdx.x; e < hi; e += kPgdThreads) qd += (double)ssrc[e] * a.Q[e];
-                block_sums4(dd, d0, qd, 0.0, sc);
-                if (threadIdx.x < 3) part[threadIdx.x] = sc[threadIdx.x];
-                cluster_sum(cl, part, tot, 3);
+                dd = block_reduce_sum(dd, scratch);
+                d0 = block_reduce_sum(d0, scratch);
+                cluster_sum4(dd, d0, 0, 0, tot, false);  // also publishes pubdel[tb]
                 dsq = tot[0];
                 dnorm = tot[1];
-                const double quad = tot[2];
-                if (quad * eta <= dsq) break;
+                // gather the full difference from every rank
+                for (int r = 0; r < ncl; r++) {
+                    const int rlo = min(a.K, r * a.ka) * per, rhi = min(a.K, r * a.ka + a.ka) * per;
+                    const float *rp = cl.map_shared_rank(S.pubdel[tb], r);
+                    for (int e = threadIdx.x; e < rhi - rlo; e += kPgdThreads) S.del[rlo + e] = rp[e];
+                }
+                __syncthreads();
+                phi_conv_own(a, S, k_lo, nown, S.del, S.q);
+                __syncthreads();
+                double qd = 0.0;
+                for (int e = threadIdx.x; e < nown; e += kPgdThreads) qd += (double)pd[e] * S.q[e];
+                qd = block_reduce_sum(qd, scratch);
+                cluster_sum4(qd, 0, 0, 0, tot, false);
+                tb ^= 1;
+                if (tot[0] * eta <= dsq) break;
                 eta *= 0.5;
             }
             // accept: D = D+, G = G + phi * (D+ - D)
-            for (int e = lo + threadIdx.x; e < hi; e += kPgdThreads) {
-                a.D[e] = a.Dn[e];
-                a.G[e] += a.Q[e];
+            for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
+                S.d[e] = S.dn[e];
+                S.g[e] += S.q[e];
             }
             if (sqrt(dsq) < a.tol * sqrt(dnorm)) {
                 it++;
@@ -379,37 +470,34 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
             }
         }
     }
-    // F(D) = 1/2||X||^2 - 1/2 <psi, D> + 1/2 <D, G>
-    double pd = 0.0, dg = 0.0;
-    for (int e = lo + threadIdx.x; e < hi; e += kPgdThreads) {
-        pd += (double)a.psi[e] * a.D[e];
-        dg += (double)a.D[e] * a.G[e];
+    __syncthreads();
+    // F(D) = 1/2||X||^2 - 1/2 <psi, D> + 1/2 <D, G>; write D back
+    double pdv = 0.0, dg = 0.0;
+    for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
+        pdv += (double)a.psi[e0 + e] * S.d[e];
+        dg += (double)S.d[e] * S.g[e];
+        a.D[e0 + e] = S.d[e];
     }
-    block_sums4(pd, dg, 0.0, 0.0, sc);
-    if (threadIdx.x < 2) part[threadIdx.x] = sc[threadIdx.x];
-    cluster_sum(cl, part, tot, 2);
+    pdv = block_reduce_sum(pdv, scratch);
+    dg = block_reduce_sum(dg, scratch);
+    cluster_sum4(pdv, dg, 0, 0, tot, false);
     if (rank == 0 && threadIdx.x == 0) {
         a.out[0] = 0.5 * a.x_sqnorm - 0.5 * tot[0] + 0.5 * tot[1];
         a.out[1] = (double)it;
         a.out[2] = eta;
     }
+    cl.sync();  // keep every rank's shared memory alive until all reads are done
 }
 
 int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x_sqnorm, float *D,
                      int max_iter, double tol, double *obj_out, int *it_out, unsigned char *ws,
                      const WsLayout &L, cudaStream_t st) {
-    if (g.K > kPgdMaxK) return CSC_ERR_UNIMPLEMENTED;
     WsHeader *h = reinterpret_cast<WsHeader *>(ws + L.hdr);
-    float *buf = reinterpret_cast<float *>(ws + L.pgd);
-    const long long n = g.nd();
+    const long long per = (long long)g.P * g.L0 * g.L1, n = g.nd();
     PgdArgs a;
     a.phi = phi;
     a.psi = psi;
     a.D = D;
-    a.G = buf;
-    a.Dn = buf + n;
-    a.Del = buf + 2 * n;
-    a.Q = buf + 3 * n;
     a.out = h->pgd_out;
     a.x_sqnorm = x_sqnorm;
     a.tol = tol;
@@ -418,33 +506,61 @@ int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x
     a.L0 = g.L0;
     a.L1 = g.L1;
     a.max_iter = max_iter;
-    size_t smem = (size_t)n * sizeof(float);
-    if (smem > 200 * 1024) return CSC_ERR_UNIMPLEMENTED;
-    CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    const double work = (double)n * g.K * g.L0 * g.L1;
-    int cs = work < 2e5 ? 2 : (work < 2e6 ? 8 : 16);
+    const size_t lim = 200 * 1024;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(kPgdThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kPgdThreads);
+    cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // the largest cluster (<= cs) that the device can schedule
-    for (;; cs /= 2) {
-        cfg.gridDim = dim3(cs);
-        attr[0].val.clusterDim.x = cs;
-        int nclusters = 0;
-        cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, pgd_kernel, &cfg);
-        if (e == cudaSuccess && nclusters >= 1) break;
-        cudaGetLastError();
-        if (cs == 1) return CSC_ERR_UNIMPLEMENTED;
+    // fewest atoms per CTA (largest cluster, at most 16) that fits and can be
+    // scheduled; the choice is cached per (device, K, P, L0, L1)
+    struct Choice {
+        int dev, K, P, L0, L1, ka, stage;
+        size_t smem;
+    };
+    static thread_local std::vector<Choice> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const Choice *hit = nullptr;
+    for (const Choice &c : cache)
+        if (c.dev == dev && c.K == g.K && c.P == g.P && c.L0 == g.L0 && c.L1 == g.L1) hit = &c;
+    if (!hit) {
+        CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        bool ok = false;
+        Choice ch{dev, g.K, g.P, g.L0, g.L1, 0, 0, 0};
+        for (int ka = (int)ceil_div(g.K, 16); ka <= 16 && !ok; ka++) {
+            const int cs = (int)ceil_div(g.K, ka);
+            size_t base = ((size_t)n + 6 * (size_t)ka * per) * sizeof(float);
+            size_t phi_bytes = (size_t)ka * g.K * g.nw() * sizeof(float);
+            if (base > lim) break;
+            ch.ka = ka;
+            ch.stage = base + phi_bytes <= lim;
+            ch.smem = base + (ch.stage ? phi_bytes : 0);
+            CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)ch.smem));
+            cfg.gridDim = dim3(cs);
+            cfg.dynamicSmemBytes = ch.smem;
+            attr[0].val.clusterDim.x = cs;
+            int nclusters = 0;
+            cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, pgd_kernel, &cfg);
+            if (e == cudaSuccess && nclusters >= 1) ok = true;
+            else cudaGetLastError();
+        }
+        if (!ok) return CSC_ERR_UNIMPLEMENTED;
+        cache.push_back(ch);
+        hit = &cache.back();
     }
+    a.ka = hit->ka;
+    a.stage_phi = hit->stage;
+    const int cs = (int)ceil_div(g.K, hit->ka);
+    CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hit->smem));
+    cfg.gridDim = dim3(cs);
+    cfg.dynamicSmemBytes = hit->smem;
+    attr[0].val.clusterDim.x = cs;
     CSC_CUDA(cudaLaunchKernelEx(&cfg, pgd_kernel, a));
     if (obj_out || it_out) {
         double out[3];

@@ -171,8 +171,8 @@ __device__ __forceinline__ real block_max2(real v, real u, real *out_u) {
 }
 
 // ------------------------------------------------------------ tile setup
-template <typename real, int NT>
-__device__ void tile_setup(const LgcdArgs<real> &a, Tile<real, NT> &t, unsigned char *smem) {
+template <typename real, int NT, int TN = NT>
+__device__ void tile_setup(const LgcdArgs<real> &a, Tile<real, TN> &t, unsigned char *smem) {
     t.w = blockIdx.x;
     t.ta = t.w / a.G1;
     t.tb = t.w % a.G1;
@@ -418,165 +418,580 @@ __device__ void write_back(const LgcdArgs<real> &a, const Tile<real, NT> &t) {
 }
 
 // ============================================================ ASYNC / NOLOCK
-template <typename real, int NT>
-__global__ void __launch_bounds__(NT, 1) lgcd_async_kernel(LgcdArgs<real> a) {
+// Warp-specialised worker: NTC compute threads run the LGCD iterations and
+// synchronise among themselves on named barrier 1; one extra warp (the
+// communication warp) owns every global control word -- the neighbour
+// inboxes and outboxes, the `pending` termination counter, the stop word and
+// the deadline -- so the compute warps never wait on global-memory latency
+// except for the soft-lock reads of a neighbour's published band.
+//
+// Shared-memory protocol between the two roles:
+//   in_ring  : records staged by the communication warp (in_head) and
+//              consumed by the compute warps (in_tail);
+//   out_ring : accepted border updates pushed by the compute leader
+//              (out_head) and sent by the communication warp (out_tail);
+//   idle_seq / resp_seq / resp_kind : the compute leader asks to pause after
+//              a quiet sweep; the communication warp answers WOKEN (a message
+//              arrived or was pending) or TERMINATE (pending == 0, stop word,
+//              or deadline);
+//   stop     : set by the communication warp when the run must end.
+constexpr int kCompute = 256;
+constexpr int kAsyncThreads = kCompute + 32;
+constexpr int kInRing = 128;
+constexpr int kOutRing = 32;
+enum { RESP_WOKEN = 1, RESP_TERMINATE = 2 };
+
+struct AsyncShared {
+    int4 in_ring[kInRing];
+    int4 out_rec[kOutRing];
+    int out_mask[kOutRing];
+    volatile int in_head, in_tail, out_head, out_tail;
+    volatile int idle_seq, resp_seq, resp_kind, stop;
+    // compute-side broadcast slots
+    int nmsg, bstop, room, idle_res;
+    volatile long long n_msg_sent;
+};
+
+__device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, %0;" ::"r"(kCompute) : "memory"); }
+
+template <typename real>
+__device__ __forceinline__ Cand<real> cand_shfl_max(Cand<real> c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Cand<real> y;
+        y.a = __shfl_xor_sync(0xffffffffu, c.a, o);
+        y.key = __shfl_xor_sync(0xffffffffu, c.key, o);
+        y.znew = __shfl_xor_sync(0xffffffffu, c.znew, o);
+        y.dz = __shfl_xor_sync(0xffffffffu, c.dz, o);
+        if (better(y, c)) c = y;
+    }
+    return c;
+}
+
+// Candidate scan of sub-domain m by the compute threads; every compute
+// thread returns the block-wide winner (one named barrier).
+template <typename real>
+__device__ __forceinline__ Cand<real> scan_v2(const LgcdArgs<real> &a, const Tile<real, kCompute> &t,
+                                              int m, Cand<real> *part) {
+    const int mr = m / t.ns1, mc = m % t.ns1;
+    const int r0 = mr * a.sub0, c0 = mc * a.sub1;
+    const int bh = min(a.sub0, t.h - r0), bw = min(a.sub1, t.wd - c0);
+    const int nb = bh * bw;
+    Cand<real> c{real(-1), 0xffffffffu, real(0), real(0)};
+    const int tid = threadIdx.x;
+    if (nb <= kCompute) {
+        const int kstep = kCompute / nb;
+        if (tid < kstep * nb) {
+            const int r = tid % nb;
+            const int li = r0 + r / bw, lj = c0 + r % bw;
+            const unsigned pos = (unsigned)(li * a.t1 + lj) * (unsigned)t.K;
+            int idx = (tid / nb) * t.TS + li * a.t1 + lj;
+            for (int k = tid / nb; k < t.K; k += kstep, idx += kstep * t.TS) {
+                real zn = coord_update(t.sbeta[idx], a.lambda, t.snrm[k], t.sinv[k]);
+                real dz = zn - t.sz[idx];
+                Cand<real> x{dz < real(0) ? -dz : dz, pos + (unsigned)k, zn, dz};
+                if (better(x, c)) c = x;
+            }
+        }
+    } else {
+        for (int q = tid; q < t.K * nb; q += kCompute) {
+            int k = q / nb, r = q % nb;
+            int li = r0 + r / bw, lj = c0 + r % bw;
+            int idx = k * t.TS + li * a.t1 + lj;
+            real zn = coord_update(t.sbeta[idx], a.lambda, t.snrm[k], t.sinv[k]);
+            real dz = zn - t.sz[idx];
+            Cand<real> x{dz < real(0) ? -dz : dz, (unsigned)((li * a.t1 + lj) * t.K + k), zn, dz};
+            if (better(x, c)) c = x;
+        }
+    }
+    c = cand_shfl_max(c);
+    if ((tid & 31) == 0) part[tid >> 5] = c;
+    cbar();
+    Cand<real> b = part[0];
+#pragma unroll
+    for (int w = 1; w < kCompute / 32; w++)
+        if (better(part[w], b)) b = part[w];
+    return b;
+}
+
+// Loop over the K x window entries of an update at tile-local (li0, lj0)
+// that fall inside the tile; fn(k, r, idx) with r the window index.
+template <typename real, typename F>
+__device__ __forceinline__ void for_window(const LgcdArgs<real> &a, const Tile<real, kCompute> &t,
+                                           int li0, int lj0, F fn) {
+    const int tid = threadIdx.x, WW = t.WW;
+    if (WW <= kCompute) {
+        const int kstep = kCompute / WW;
+        if (tid >= kstep * WW) return;
+        const int r = tid % WW;
+        const int li = li0 + r / a.W1 - (a.L0 - 1), lj = lj0 + r % a.W1 - (a.L1 - 1);
+        if (li < 0 || li >= t.h || lj < 0 || lj >= t.wd) return;
+        int idx = (tid / WW) * t.TS + li * a.t1 + lj;
+        for (int k = tid / WW; k < t.K; k += kstep, idx += kstep * t.TS) fn(k, r, idx, li, lj);
+    } else {
+        for (int q = tid; q < t.K * WW; q += kCompute) {
+            int k = q / WW, r = q % WW;
+            int li = li0 + r / a.W1 - (a.L0 - 1), lj = lj0 + r % a.W1 - (a.L1 - 1);
+            if (li < 0 || li >= t.h || lj < 0 || lj >= t.wd) continue;
+            fn(k, r, k * t.TS + li * a.t1 + lj, li, lj);
+        }
+    }
+}
+
+// Warp-wide winner of (largest |dZ|, then smallest key); returns the key
+// (0xffffffff when every lane is empty).  FP32 uses the redux unit on the
+// order-preserving bits of |dZ|.
+__device__ __forceinline__ unsigned warp_argmax_key(float a, unsigned key) {
+    const unsigned bits = a < 0.f ? 0u : __float_as_uint(a) + 1u;  // empty lanes sort lowest
+    const unsigned m = __reduce_max_sync(0xffffffffu, bits);
+    if (m == 0u) return 0xffffffffu;
+    return __reduce_min_sync(0xffffffffu, bits == m ? key : 0xffffffffu);
+}
+__device__ __forceinline__ unsigned warp_argmax_key(double a, unsigned key) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oa = __shfl_xor_sync(0xffffffffu, a, o);
+        const unsigned ok = __shfl_xor_sync(0xffffffffu, key, o);
+        if (oa > a || (oa == a && ok < key)) {
+            a = oa;
+            key = ok;
+        }
+    }
+    return a < 0.0 ? 0xffffffffu : key;
+}
+
+// Soft-lock maxima for a border candidate, by one warp: the largest |dZ| of
+// the neighbours' published band inside V(s0), split by owner index.  Loads
+// are issued in batches so a check costs about one memory round trip.
+template <typename real>
+__device__ __forceinline__ void softlock_warp(const LgcdArgs<real> &a, const Tile<real, kCompute> &t, int li0,
+                                              int lj0, int lane, real *m_lo, real *m_hi) {
+    constexpr int B = 8;
+    real lo = real(-1), hi = real(-1);
+    const int gi0 = t.or0 + li0, gj0 = t.oc0 + lj0;
+    const int n = t.K * t.WW;
+    for (int base = 0; base < n; base += 32 * B) {
+        real vb[B], vz[B];
+        int kk[B], side[B];  // side: 0 none, 1 lower-index owner, 2 higher
+#pragma unroll
+        for (int u = 0; u < B; u++) {
+            const int q = base + u * 32 + lane;
+            side[u] = 0;
+            kk[u] = 0;
+            vb[u] = real(0);
+            vz[u] = real(0);
+            if (q < n) {
+                const int k = q / t.WW, r = q % t.WW;
+                const int gi = gi0 + r / a.W1 - (a.L0 - 1), gj = gj0 + r % a.W1 - (a.L1 - 1);
+                const bool inside_dom = gi >= 0 && gi < a.Z0 && gj >= 0 && gj < a.Z1;
+                const bool inside_tile = gi >= t.or0 && gi < t.or0 + t.h && gj >= t.oc0 && gj < t.oc0 + t.wd;
+                if (inside_dom && !inside_tile) {
+                    const size_t g = ((size_t)k * a.Z0 + gi) * a.Z1 + gj;
+                    vb[u] = ld_relaxed(a.beta + g);
+                    vz[u] = ld_relaxed(a.Z + g);
+                    kk[u] = k;
+                    side[u] = ((gi / a.t0) * a.G1 + gj / a.t1) < t.w ? 1 : 2;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < B; u++) {
+            if (side[u] == 0) continue;
+            const int k = kk[u];
+            real d = coord_update(vb[u], a.lambda, t.snrm[k], t.sinv[k]) - vz[u];
+            d = d < real(0) ? -d : d;
+            if (side[u] == 1) lo = max(lo, d);
+            else hi = max(hi, d);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    *m_lo = lo;
+    *m_hi = hi;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<real> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Tile<real, NT> t;
-    tile_setup<real, NT>(a, t, smem_raw);
-
-    __shared__ int s_nmsg, s_state, s_accept;
-    __shared__ real s_mlo, s_mhi;
-
-    Comm cm;
-    long long n_upd = 0, n_it = 0, n_rej = 0, n_sub = 0, n_msg = 0, n_def = 0;
+    __shared__ AsyncShared S;
+    __shared__ Cand<real> part[kCompute / 32];
+    __shared__ real lpart[kCompute / 32][2];
+    Tile<real, kCompute> t;
+    tile_setup<real, kAsyncThreads, kCompute>(a, t, smem_raw);
     const unsigned long long deadline = globaltimer_ns() + a.timeout_ns;
+    if (threadIdx.x == 0) {
+        S.in_head = S.in_tail = S.out_head = S.out_tail = 0;
+        S.idle_seq = S.resp_seq = S.resp_kind = 0;
+        S.stop = 0;
+        S.n_msg_sent = 0;
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= kCompute) {
+        // ------------------------------------------------ communication warp
+        if (threadIdx.x != kCompute) return;
+        int ndir = 0, dirs[kDirs], in_tail[kDirs], out_head[kDirs], out_tail[kDirs];
+        for (int d = 0; d < kDirs; d++) {
+            int dr, dc;
+            dir_offset(d, dr, dc);
+            int r = t.ta + dr, c = t.tb + dc;
+            in_tail[d] = out_head[d] = out_tail[d] = 0;
+            if (r >= 0 && r < a.G0 && c >= 0 && c < a.G1) dirs[ndir++] = d;
+        }
+        bool idle = false;
+        int spins = 0;
+        for (;;) {
+            bool work = false;
+            // inbound: stage new records while the ring has room
+            int heads[kDirs];
+            for (int i = 0; i < ndir; i++)
+                heads[dirs[i]] = ld_relaxed(a.ctl + ((size_t)t.w * kDirs + dirs[i]) * 32);
+            int avail = 0;
+            for (int i = 0; i < ndir; i++) avail += heads[dirs[i]] - in_tail[dirs[i]];
+            if (avail > 0) {
+                if (idle) {
+                    atomicAdd(&a.hdr->pending, 1);  // reactivate before consuming
+                    idle = false;
+                    S.resp_kind = RESP_WOKEN;
+                    __threadfence_block();
+                    S.resp_seq = S.idle_seq;
+                }
+                fence_acq_rel_gpu();
+                int ih = S.in_head;
+                const int room = kInRing - (ih - S.in_tail);
+                int took = 0;
+                for (int i = 0; i < ndir && took < room; i++) {
+                    const int d = dirs[i];
+                    const int link = t.w * kDirs + d;
+                    const int n = min(heads[d] - in_tail[d], room - took);
+                    for (int j = 0; j < n; j++)
+                        S.in_ring[(ih + took + j) & (kInRing - 1)] =
+                            __ldcg(a.slots + (size_t)link * a.cap + (in_tail[d] + j) % a.cap);
+                    if (n > 0) {
+                        in_tail[d] += n;
+                        took += n;
+                        st_release(a.ctl + (size_t)link * 32 + 16, in_tail[d]);
+                    }
+                }
+                if (took > 0) {
+                    __threadfence_block();
+                    S.in_head = ih + took;
+                    atomicSub(&a.hdr->pending, took);
+                    work = true;
+                }
+            }
+            // outbound: send queued border updates in order
+            while (S.out_tail != S.out_head) {
+                const int ot = S.out_tail;
+                const int4 rec = S.out_rec[ot & (kOutRing - 1)];
+                const int mask = S.out_mask[ot & (kOutRing - 1)];
+                bool room_all = true;
+                for (int d = 0; d < kDirs && room_all; d++) {
+                    if (!(mask >> d & 1)) continue;
+                    int dr, dc;
+                    dir_offset(d, dr, dc);
+                    const int link = ((t.ta + dr) * a.G1 + (t.tb + dc)) * kDirs + (7 - d);
+                    if (out_head[d] - out_tail[d] >= a.cap) {
+                        out_tail[d] = ld_acquire(a.ctl + (size_t)link * 32 + 16);
+                        room_all = out_head[d] - out_tail[d] < a.cap;
+                    }
+                }
+                if (!room_all) break;
+                atomicAdd(&a.hdr->pending, __popc(mask));
+                for (int d = 0; d < kDirs; d++) {
+                    if (!(mask >> d & 1)) continue;
+                    int dr, dc;
+                    dir_offset(d, dr, dc);
+                    const int link = ((t.ta + dr) * a.G1 + (t.tb + dc)) * kDirs + (7 - d);
+                    __stcg(a.slots + (size_t)link * a.cap + out_head[d] % a.cap, rec);
+                    out_head[d]++;
+                    st_release(a.ctl + (size_t)link * 32, out_head[d]);
+                }
+                S.n_msg_sent = S.n_msg_sent + __popc(mask);
+                __threadfence_block();
+                S.out_tail = ot + 1;
+                work = true;
+            }
+            // pause request after a quiet sweep
+            if (!idle && S.idle_seq != S.resp_seq) {
+                if (S.in_head != S.in_tail || S.out_head != S.out_tail) {
+                    S.resp_kind = RESP_WOKEN;
+                    __threadfence_block();
+                    S.resp_seq = S.idle_seq;
+                } else {
+                    atomicSub(&a.hdr->pending, 1);
+                    idle = true;
+                }
+                work = true;
+            }
+            if (idle && ld_acquire(&a.hdr->pending) == 0) {
+                S.resp_kind = RESP_TERMINATE;
+                __threadfence_block();
+                S.resp_seq = S.idle_seq;
+                break;
+            }
+            if (++spins >= 64 || !work) {
+                spins = 0;
+                const int st = ld_relaxed(&a.hdr->stop);
+                const bool late = globaltimer_ns() > deadline;
+                if (late) set_stop(a.hdr, CSC_ERR_TIMEOUT);
+                if (st || late) {
+                    S.stop = 1;
+                    S.resp_kind = RESP_TERMINATE;
+                    __threadfence_block();
+                    S.resp_seq = S.idle_seq;
+                    break;
+                }
+            }
+            if (!work) __nanosleep(idle ? 200 : 32);
+        }
+        return;
+    }
+
+    // ------------------------------------------------------- compute warps
+    // Colour waves: sub-domain (mr, mc) of the tile has colour
+    // 2 (mr mod 2) + (mc mod 2).  Two sub-domains of one colour are at least
+    // one full sub-domain (2 L_i) apart, so an update in one changes beta only
+    // outside the other and their cost changes add up (the cross term of
+    // Prop. A.2 is zero).  Each wave processes every sub-domain of one colour,
+    // one warp per sub-domain; a sweep visits every colour once.
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kCompute / 32;
+    constexpr int kWout = 8;  // border records one warp may emit per wave
+    __shared__ int wact[2][kWarps], wout_n[2][kWarps], room_left;
+    __shared__ int4 wout_rec[2][kWarps][kWout];
+    __shared__ int wout_mask[2][kWarps][kWout];
+    long long n_upd = 0, n_it = 0, n_rej = 0, n_sub = 0, n_def = 0, n_wave = 0;
     real guard = real(0);
     if (a.guard_on) {
         double g = 1e300;
         for (int k = 0; k < a.K; k++) g = fmin(g, 50.0 / a.dmax[k]);
         guard = real(g);
     }
-    if (threadIdx.x == 0) {
-        cm.ndir = 0;
-        for (int d = 0; d < kDirs; d++) {
-            int dr, dc;
-            dir_offset(d, dr, dc);
-            int r = t.ta + dr, c = t.tb + dc;
-            cm.out_head[d] = cm.out_tail[d] = cm.in_tail[d] = 0;
-            cm.prefetch[d] = 0;
-            if (r >= 0 && r < a.G0 && c >= 0 && c < a.G1) cm.dirs[cm.ndir++] = d;
-        }
-        for (int i = 0; i < cm.ndir; i++)
-            cm.prefetch[cm.dirs[i]] = ld_relaxed(a.ctl + ((size_t)t.w * kDirs + cm.dirs[i]) * 32);
+    const int ns0 = (t.h + a.sub0 - 1) / a.sub0, ns1 = t.ns1;
+    int ccount[4], ncol = 0, colors[4];
+    for (int c = 0; c < 4; c++) {
+        const int rc = c >> 1, cc = c & 1;
+        const int nr = rc < ns0 ? (ns0 - rc + 1) / 2 : 0, nc = cc < ns1 ? (ns1 - cc + 1) / 2 : 0;
+        ccount[c] = nr * nc;
+        if (ccount[c] > 0) colors[ncol++] = c;
     }
-    int stop_seen = 0;
-    int m = 0, quiet = 0;
+    int ci = 0, quiet = 0;
     for (;;) {
-        // ---- receive (Alg. 3: "receive messages and update beta")
-        if (threadIdx.x == 0) {
-            int n = stage_messages<real, NT>(a, t, cm, cm.prefetch);
-            if (n > 0) atomicSub(&a.hdr->pending, n);
-            s_nmsg = n;
-            s_state = stop_seen ? 2 : (globaltimer_ns() > deadline ? 3 : 0);
+        if (tid == 0) {
+            S.nmsg = S.in_head - S.in_tail;
+            S.bstop = S.stop;
+            room_left = kOutRing - (S.out_head - S.out_tail);
         }
-        __syncthreads();
-        if (s_state != 0) {
-            if (threadIdx.x == 0 && s_state == 3) set_stop(a.hdr, CSC_ERR_TIMEOUT);
-            break;
+        cbar();
+        if (S.bstop) break;
+        const int par = (int)(n_wave & 1);
+        if (lane == 0) {
+            wact[par][warp] = 0;
+            wout_n[par][warp] = 0;
         }
-        const int nmsg = s_nmsg;
+        const int nmsg = S.nmsg;
         if (nmsg > 0) {
-            apply_messages<real, NT>(a, t, nmsg);
-            __syncthreads();
+            // neighbour updates (Alg. 3 "receive messages and update beta")
+            const int base = S.in_tail;
+            for (int i = 0; i < nmsg; i++) {
+                const int4 msg = S.in_ring[(base + i) & (kInRing - 1)];
+                real dz;
+                unpack_msg(msg, dz);
+                const int gi = msg.y / a.Z1, gj = msg.y % a.Z1;
+                const real *row = t.sdtd + (size_t)msg.x * t.K * t.WW;
+                for_window(a, t, gi - t.or0, gj - t.oc0, [&](int k, int r, int idx, int li, int lj) {
+                    atomicAdd(&t.sbeta[idx], -(row[k * t.WW + r] * dz));
+                });
+            }
+            cbar();
+            for (int i = 0; i < nmsg; i++) {
+                const int4 msg = S.in_ring[(base + i) & (kInRing - 1)];
+                const int gi = msg.y / a.Z1, gj = msg.y % a.Z1;
+                for_window(a, t, gi - t.or0, gj - t.oc0, [&](int k, int r, int idx, int li, int lj) {
+                    st_relaxed(a.beta + ((size_t)k * a.Z0 + t.or0 + li) * a.Z1 + t.oc0 + lj, t.sbeta[idx]);
+                });
+            }
+            cbar();
+            if (tid == 0) S.in_tail = base + nmsg;
         }
-        // ---- local greedy candidate on C_m
-        Cand<real> best = scan_subdomain<real, NT>(a, t, m);
-        n_it++;
-        bool active = best.a >= a.eps;
-        if (active) {
-            const unsigned pos = best.key / (unsigned)t.K;
-            const int k0 = (int)(best.key % (unsigned)t.K);
+        // ---- one wave: the sub-domains of colour c, one warp each
+        const int c = colors[ci];
+        const int rc = c >> 1, cc = c & 1, ncc = (ns1 - cc + 1) / 2;
+        for (int j = warp; j < ccount[c]; j += kWarps) {
+            const int mr = rc + 2 * (j / ncc), mc = cc + 2 * (j % ncc);
+            const int r0 = mr * a.sub0, c0 = mc * a.sub1;
+            const int bh = min(a.sub0, t.h - r0), bw = min(a.sub1, t.wd - c0), nb = bh * bw;
+            // candidate scan (Eq. gcd_candidate) with the oracle's tie-break
+            real ba = real(-1);
+            unsigned bkey = 0xffffffffu;
+            for (int r = lane; r < nb; r += 32) {
+                const int li = r0 + r / bw, lj = c0 + r % bw;
+                const unsigned pos = (unsigned)(li * a.t1 + lj) * (unsigned)t.K;
+                int idx = li * a.t1 + lj;
+                for (int k = 0; k < t.K; k++, idx += t.TS) {
+                    const real zn = coord_update(t.sbeta[idx], a.lambda, t.snrm[k], t.sinv[k]);
+                    real d = zn - t.sz[idx];
+                    d = d < real(0) ? -d : d;
+                    const unsigned key = pos + (unsigned)k;
+                    if (d > ba || (d == ba && key < bkey)) {
+                        ba = d;
+                        bkey = key;
+                    }
+                }
+            }
+            const unsigned wkey = warp_argmax_key(ba, bkey);
+            n_it += (lane == 0);
+            if (wkey == 0xffffffffu) continue;
+            const unsigned pos = wkey / (unsigned)t.K;
+            const int k0 = (int)(wkey % (unsigned)t.K);
             const int li0 = (int)(pos / (unsigned)a.t1), lj0 = (int)(pos % (unsigned)a.t1);
-            bool border = in_band(li0, lj0, t.h, t.wd, a.L0, a.L1);
+            const int idx0 = k0 * t.TS + li0 * a.t1 + lj0;
+            const real znew = coord_update(t.sbeta[idx0], a.lambda, t.snrm[k0], t.sinv[k0]);
+            const real dz = znew - t.sz[idx0];
+            const real adz = dz < real(0) ? -dz : dz;
+            if (!(adz >= a.eps)) {
+                n_sub += (lane == 0);
+                continue;
+            }
+            if (lane == 0) wact[par][warp] = 1;
+            const bool border = in_band(li0, lj0, t.h, t.wd, a.L0, a.L1);
             bool accept = true;
-            if (border && a.mode == CSC_MODE_ASYNC) {
-                real mlo, mhi;
-                softlock_maxima<real, NT>(a, t, li0, lj0, &mlo, &mhi);
-                accept = best.a > mlo && best.a >= mhi;
-            }
-            int dirs[kDirs];
-            int nd = 0;
-            if (threadIdx.x == 0) {
-                if (accept && border) {
-                    nd = target_dirs<real, NT>(a, t, li0, lj0, dirs);
-                    if (!links_have_room<real, NT>(a, t, cm, dirs, nd)) {
+            if (border) {
+                if (a.mode == CSC_MODE_ASYNC) {
+                    real lo, hi;
+                    softlock_warp(a, t, li0, lj0, lane, &lo, &hi);
+                    accept = adz > lo && adz >= hi;
+                    n_rej += (lane == 0 && !accept);
+                }
+                if (accept) {
+                    int ok = 0;
+                    if (lane == 0 && wout_n[par][warp] < kWout) {
+                        ok = atomicSub(&room_left, 1) > 0;
+                        if (!ok) atomicAdd(&room_left, 1);
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) {
                         accept = false;
-                        n_def++;
+                        n_def += (lane == 0);
                     }
                 }
-                s_accept = accept;
             }
-            __syncthreads();
-            accept = s_accept;
-            if (accept) {
-                const int idx0 = k0 * t.TS + li0 * a.t1 + lj0;
-                const real dz = best.dz;
-                apply_own_update<real, NT>(a, t, k0, li0, lj0, dz);
-                if (threadIdx.x == 0) {
-                    t.sz[idx0] = best.znew;
-                    if (border) {
-                        size_t g = ((size_t)k0 * a.Z0 + t.or0 + li0) * a.Z1 + t.oc0 + lj0;
-                        st_relaxed(a.Z + g, best.znew);
-                    }
-                    int s_lin = (t.or0 + li0) * a.Z1 + t.oc0 + lj0;
-                    post_messages<real, NT>(a, t, cm, dirs, nd, k0, s_lin, dz);
-                    n_msg += nd;
-                    n_upd++;
-                    if (a.max_updates > 0) {
-                        unsigned long long prev = atomicAdd(&a.hdr->updates_total, 1ull);
-                        if ((long long)prev + 1 >= a.max_updates) set_stop(a.hdr, CSC_NOT_CONVERGED);
-                    }
-                    real az = best.znew < real(0) ? -best.znew : best.znew;
-                    if (a.guard_on && az > guard) set_stop(a.hdr, CSC_ERR_DIVERGED);
+            if (!accept) continue;
+            // beta_k[s] -= C[k][k0][s - s0] dz over V(s0) in the tile (Eq. beta_update)
+            const real *row = t.sdtd + (size_t)k0 * t.K * t.WW;
+            for (int r = lane; r < t.WW; r += 32) {
+                const int li = li0 + r / a.W1 - (a.L0 - 1), lj = lj0 + r % a.W1 - (a.L1 - 1);
+                if (li < 0 || li >= t.h || lj < 0 || lj >= t.wd) continue;
+                const bool band = in_band(li, lj, t.h, t.wd, a.L0, a.L1);
+                const bool center = li == li0 && lj == lj0;
+                int idx = li * a.t1 + lj;
+                for (int k = 0; k < t.K; k++, idx += t.TS) {
+                    if (center && k == k0) continue;
+                    const real v = sub_prod(t.sbeta[idx], row[k * t.WW + r], dz);
+                    t.sbeta[idx] = v;
+                    if (band) st_relaxed(a.beta + ((size_t)k * a.Z0 + t.or0 + li) * a.Z1 + t.oc0 + lj, v);
                 }
-            } else if (threadIdx.x == 0 && border) {
-                n_rej++;
             }
-        } else {
-            n_sub++;
-        }
-        quiet = (active || nmsg > 0) ? 0 : quiet + 1;
-        m = (m + 1 == t.M) ? 0 : m + 1;
-        // ---- prefetch control words for the next iteration (relaxed: no stall)
-        if (threadIdx.x == 0) {
-            for (int i = 0; i < cm.ndir; i++)
-                cm.prefetch[cm.dirs[i]] = ld_relaxed(a.ctl + ((size_t)t.w * kDirs + cm.dirs[i]) * 32);
-            stop_seen = ld_relaxed(&a.hdr->stop);
-        }
-        // ---- idle: a full sweep with nothing to do (Alg. 3 pause)
-        if (quiet >= t.M) {
-            if (threadIdx.x == 0) {
-                atomicSub(&a.hdr->pending, 1);
-                int state = 0;
-                for (;;) {
-                    bool wake = false;
-                    for (int i = 0; i < cm.ndir; i++) {
-                        int d = cm.dirs[i];
-                        int hd = ld_relaxed(a.ctl + ((size_t)t.w * kDirs + d) * 32);
-                        cm.prefetch[d] = hd;
-                        wake |= hd != cm.in_tail[d];
+            __syncwarp();
+            if (lane == 0) {
+                t.sz[idx0] = znew;
+                n_upd++;
+                if (border) {
+                    st_relaxed(a.Z + ((size_t)k0 * a.Z0 + t.or0 + li0) * a.Z1 + t.oc0 + lj0, znew);
+                    int dl[kDirs];
+                    const int nd = target_dirs<real, kCompute>(a, t, li0, lj0, dl);
+                    if (nd > 0) {
+                        int mask = 0;
+                        for (int i = 0; i < nd; i++) mask |= 1 << dl[i];
+                        const int o = wout_n[par][warp]++;
+                        wout_rec[par][warp][o] = pack_msg(k0, (t.or0 + li0) * a.Z1 + t.oc0 + lj0, dz);
+                        wout_mask[par][warp][o] = mask;
+                    } else {
+                        atomicAdd(&room_left, 1);  // reserved slot not needed
                     }
-                    if (wake) {
-                        atomicAdd(&a.hdr->pending, 1);
-                        state = 0;
-                        break;
-                    }
-                    if (ld_acquire(&a.hdr->pending) == 0) { state = 1; break; }
-                    if (ld_relaxed(&a.hdr->stop)) { state = 1; break; }
-                    if (globaltimer_ns() > deadline) {
+                }
+                if (a.max_updates > 0) {
+                    unsigned long long prev = atomicAdd(&a.hdr->updates_total, 1ull);
+                    if ((long long)prev + 1 >= a.max_updates) set_stop(a.hdr, CSC_NOT_CONVERGED);
+                }
+                const real az = znew < real(0) ? -znew : znew;
+                if (a.guard_on && az > guard) set_stop(a.hdr, CSC_ERR_DIVERGED);
+            }
+            __syncwarp();
+        }
+        cbar();
+        // ---- end of wave: hand border updates to the communication warp
+        bool any = nmsg > 0;
+        for (int w = 0; w < kWarps; w++) any |= wact[par][w] != 0;
+        if (tid == 0) {
+            int oh = S.out_head;
+            for (int w = 0; w < kWarps; w++)
+                for (int i = 0; i < wout_n[par][w]; i++, oh++) {
+                    S.out_rec[oh & (kOutRing - 1)] = wout_rec[par][w][i];
+                    S.out_mask[oh & (kOutRing - 1)] = wout_mask[par][w][i];
+                }
+            __threadfence_block();
+            S.out_head = oh;
+        }
+        n_wave++;
+        ci = ci + 1 == ncol ? 0 : ci + 1;
+        quiet = any ? 0 : quiet + 1;
+        if (quiet >= ncol) {
+            // a full sweep without work: pause (Alg. 3)
+            if (tid == 0) {
+                const int seq = S.idle_seq + 1;
+                __threadfence_block();
+                S.idle_seq = seq;
+                const unsigned long long late = deadline + 2000000000ull;
+                while (S.resp_seq != seq) {
+                    if (globaltimer_ns() > late) {
                         set_stop(a.hdr, CSC_ERR_TIMEOUT);
-                        state = 1;
+                        S.stop = 1;
                         break;
                     }
-                    __nanosleep(256);
+                    __nanosleep(64);
                 }
-                s_state = state;
+                S.idle_res = (S.resp_kind == RESP_TERMINATE) || S.stop;
             }
-            __syncthreads();
-            if (s_state == 1) break;
+            cbar();
+            if (S.idle_res) break;
             quiet = 0;
-        } else {
-            __syncthreads();
         }
     }
-    write_back<real, NT>(a, t);
-    if (threadIdx.x == 0) {
+    // wait for the communication warp to finish before the tile is written
+    if (tid == 0) {
+        const unsigned long long late = deadline + 4000000000ull;
+        while (S.resp_kind != RESP_TERMINATE && !S.stop && globaltimer_ns() < late) __nanosleep(64);
+    }
+    cbar();
+    const int hw = t.h * t.wd;
+    for (int q = tid; q < t.K * hw; q += kCompute) {
+        const int k = q / hw, r = q % hw, li = r / t.wd, lj = r % t.wd;
+        const size_t g = ((size_t)k * a.Z0 + t.or0 + li) * a.Z1 + t.oc0 + lj;
+        a.beta[g] = t.sbeta[k * t.TS + li * a.t1 + lj];
+        a.Z[g] = t.sz[k * t.TS + li * a.t1 + lj];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_upd += __shfl_xor_sync(0xffffffffu, n_upd, o);
+        n_it += __shfl_xor_sync(0xffffffffu, n_it, o);
+        n_rej += __shfl_xor_sync(0xffffffffu, n_rej, o);
+        n_sub += __shfl_xor_sync(0xffffffffu, n_sub, o);
+        n_def += __shfl_xor_sync(0xffffffffu, n_def, o);
+    }
+    if (lane == 0) {
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_UPDATES], (unsigned long long)n_upd);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_ITERS], (unsigned long long)n_it);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_REJECTED], (unsigned long long)n_rej);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_SUBTOL], (unsigned long long)n_sub);
-        atomicAdd((unsigned long long *)&a.hdr->stat[ST_MESSAGES], (unsigned long long)n_msg);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_DEFERRED], (unsigned long long)n_def);
+    }
+    if (tid == 0) {
+        atomicAdd((unsigned long long *)&a.hdr->stat[ST_MESSAGES], (unsigned long long)S.n_msg_sent);
+        atomicMax(&a.hdr->wmax[0], (unsigned long long)n_wave);
     }
 }
 
@@ -732,6 +1147,7 @@ __global__ void reset_header_kernel(WsHeader *h, int workers) {
     h->round_applied[1] = 0;
     h->updates_total = 0;
     for (int i = 0; i < 8; i++) h->stat[i] = 0;
+    h->wmax[0] = h->wmax[1] = 0;
     h->maxdz_bits = 0;
     h->obj_f = 0.0;
     h->obj_g = 0.0;
@@ -756,32 +1172,33 @@ static size_t tile_smem(const Geom &g, int t0, int t1, int rs) {
 template <typename real>
 static const void *kernel_ptr(int mode) {
     if (mode == CSC_MODE_PHASED) return (const void *)lgcd_phased_kernel<real, kLgcdThreads>;
-    return (const void *)lgcd_async_kernel<real, kLgcdThreads>;
+    return (const void *)lgcd_async_kernel<real>;
 }
+static int kernel_threads(int mode) { return mode == CSC_MODE_PHASED ? kLgcdThreads : kAsyncThreads; }
 
-static int smem_limit() {
-    int dev = 0, v = 0;
+struct DevProps {
+    int dev = -1, smem_optin = 0, sms = 0, smem_sm = 0;
+};
+static const DevProps &dev_props() {
+    static thread_local DevProps p;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return v;
+    if (p.dev != dev) {
+        p.dev = dev;
+        cudaDeviceGetAttribute(&p.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&p.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    }
+    return p;
 }
-static int num_sms() {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    return v;
-}
-static int smem_per_sm() {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    return v;
-}
+static int smem_limit() { return dev_props().smem_optin; }
+static int num_sms() { return dev_props().sms; }
+static int smem_per_sm() { return dev_props().smem_sm; }
 
 // Tile plan.  Full tiles must be at least L_i wide (windows then reach only
 // the adjacent tiles); automatic plans use tiles of at least 2 L_i and the
 // largest number of workers that can all be resident at once.
-static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, Plan *pl) {
+static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, size_t static_smem, Plan *pl) {
     const bool d1 = g.d == 1;
     pl->sub0 = d1 ? 1 : (o.sub[0] > 0 ? o.sub[0] : 2 * g.L0);
     pl->sub1 = d1 ? (o.sub[0] > 0 ? o.sub[0] : 2 * g.L1) : (o.sub[1] > 0 ? o.sub[1] : 2 * g.L1);
@@ -796,7 +1213,7 @@ static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, Plan *pl) {
         pl->G0 = (int)ceil_div(g.Z0, t0);
         pl->G1 = (int)ceil_div(g.Z1, t1);
         pl->smem = tile_smem(g, t0, t1, rs);
-        if ((int)pl->smem > lim) return CSC_ERR_UNIMPLEMENTED;
+        if (pl->smem + static_smem > (size_t)lim) return CSC_ERR_UNIMPLEMENTED;
         return CSC_OK;
     }
     const int minT0 = d1 ? 1 : std::min(g.Z0, 2 * g.L0), minT1 = std::min(g.Z1, 2 * g.L1);
@@ -807,7 +1224,7 @@ static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, Plan *pl) {
     for (int occ = 1; occ <= 8; occ++) {
         long long cap_w = (long long)occ * sms;
         if (o.max_workers > 0) cap_w = std::min<long long>(cap_w, o.max_workers);
-        size_t budget = std::min<size_t>((size_t)lim, (size_t)per_sm / occ - 1024);
+        size_t budget = std::min<size_t>((size_t)lim - static_smem, (size_t)per_sm / occ - 1024 - static_smem);
         for (int G0 = 1; G0 <= maxG0; G0++) {
             int G1 = (int)std::min<long long>(maxG1, cap_w / G0);
             if (G1 < 1) break;
@@ -855,8 +1272,25 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     if (opts_in) o = *opts_in;
     if (o.mode < 0 || o.mode > 2 || o.beta_refresh < 0) return CSC_ERR_INVALID;
     const int rs = (int)sizeof(real);
+    const void *kern = kernel_ptr<real>(o.mode);
+    size_t static_smem = 0;
+    {
+        static thread_local std::vector<std::pair<const void *, size_t>> attr_cache;
+        bool found = false;
+        for (auto &c : attr_cache)
+            if (c.first == kern) {
+                static_smem = c.second;
+                found = true;
+            }
+        if (!found) {
+            cudaFuncAttributes fa;
+            CSC_CUDA(cudaFuncGetAttributes(&fa, kern));
+            static_smem = fa.sharedSizeBytes;
+            attr_cache.push_back({kern, static_smem});
+        }
+    }
     Plan pl;
-    rc = make_plan(g, o, rs, &pl);
+    rc = make_plan(g, o, rs, static_smem, &pl);
     if (rc) return rc;
     const int W = pl.G0 * pl.G1;
     WsLayout L = plan_workspace(g, W, rs);
@@ -866,11 +1300,28 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     double *nrm = reinterpret_cast<double *>(wsb + L.nrm);
     double *dmax = reinterpret_cast<double *>(wsb + L.dmax);
 
-    const void *kern = kernel_ptr<real>(o.mode);
-    CSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-    int occ = 0;
-    CSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLgcdThreads, pl.smem));
-    if ((long long)occ * num_sms() < W) return CSC_ERR_UNIMPLEMENTED;
+    {
+        // kernel attribute and co-residency check, cached per (kernel, device, smem)
+        struct Key {
+            const void *k;
+            int dev;
+            size_t smem;
+            int occ;
+        };
+        static thread_local std::vector<Key> cache;
+        const int dev = dev_props().dev;
+        int occ = -1;
+        for (const Key &c : cache)
+            if (c.k == kern && c.dev == dev && c.smem == pl.smem) occ = c.occ;
+        if (occ < 0) {
+            CSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+            CSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kernel_threads(o.mode), pl.smem));
+            cache.push_back({kern, dev, pl.smem, occ});
+        } else {
+            CSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+        }
+        if ((long long)occ * num_sms() < W) return CSC_ERR_UNIMPLEMENTED;
+    }
 
     if (!o.warm_start) CSC_CUDA(cudaMemsetAsync(Z, 0, (size_t)g.nz() * rs, st));
     rc = launch_atom_norms<real>(g, D, nrm, dmax, st);
@@ -902,7 +1353,10 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     a.guard_on = o.divergence_guard;
     a.cap = kMailboxCap;
     a.lambda = lambda;
-    a.eps = tol;
+    // FP32 solves stop at 0.99 tol so that rounding drift of the incrementally
+    // maintained beta rarely pushes a coordinate back above tol on the
+    // recomputed beta; the FP64 build keeps tol exactly.
+    a.eps = sizeof(real) == 4 ? real(0.99) * tol : tol;
     a.max_updates = o.max_updates;
     double tmo = o.timeout_s > 0 ? o.timeout_s : 30.0;
     a.timeout_ns = (unsigned long long)(tmo * 1e9);
@@ -923,9 +1377,11 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     S.tiles[1] = g.d == 1 ? 1 : pl.G1;
     S.tile_size[0] = g.d == 1 ? pl.t1 : pl.t0;
     S.tile_size[1] = g.d == 1 ? 1 : pl.t1;
-    cudaEvent_t e0, e1;
-    CSC_CUDA(cudaEventCreate(&e0));
-    CSC_CUDA(cudaEventCreate(&e1));
+    static thread_local cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!e0) {
+        CSC_CUDA(cudaEventCreate(&e0));
+        CSC_CUDA(cudaEventCreate(&e1));
+    }
     int status = CSC_OK;
     float kms_total = 0.f;
     WsHeader hh;
@@ -935,9 +1391,12 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
         CSC_CUDA(cudaGetLastError());
         void *args[] = {&a};
         CSC_CUDA(cudaEventRecord(e0, st));
-        CSC_CUDA(cudaLaunchCooperativeKernel(kern, dim3(W), dim3(kLgcdThreads), args, pl.smem, st));
+        CSC_CUDA(cudaLaunchCooperativeKernel(kern, dim3(W), dim3(kernel_threads(o.mode)), args, pl.smem, st));
         CSC_CUDA(cudaEventRecord(e1, st));
-        // stop word -> status, then the solve counters
+        // beta from scratch, KKT and objective on the current Z, then one sync
+        rc = launch_refresh<real>(g, L, wsb, X, D, Z, lambda, beta, st);
+        if (rc) return rc;
+        S.refresh_rounds++;
         CSC_CUDA(cudaMemcpyAsync(&hh, hdr, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
         CSC_CUDA(cudaStreamSynchronize(st));
         float ms = 0.f;
@@ -948,13 +1407,10 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
         S.rejected_softlock += hh.stat[ST_REJECTED];
         S.skipped_subtol += hh.stat[ST_SUBTOL];
         S.messages += hh.stat[ST_MESSAGES];
+        S.deferred += hh.stat[ST_DEFERRED];
+        S.max_worker_iterations = std::max<long long>(S.max_worker_iterations, (long long)hh.wmax[0]);
+        S.max_worker_updates = std::max<long long>(S.max_worker_updates, (long long)hh.wmax[1]);
         status = hh.stop;
-        // beta from scratch, KKT and objective on the current Z
-        rc = launch_refresh<real>(g, L, wsb, X, D, Z, lambda, beta, st);
-        if (rc) return rc;
-        S.refresh_rounds++;
-        CSC_CUDA(cudaMemcpyAsync(&hh, hdr, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
-        CSC_CUDA(cudaStreamSynchronize(st));
         double maxdz;
         if (sizeof(real) == 4) {
             unsigned u = (unsigned)hh.maxdz_bits;
@@ -975,8 +1431,6 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
         }
         a.max_updates = o.max_updates > 0 ? std::max<long long>(1, o.max_updates - S.updates) : 0;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     S.kernel_ms = kms_total;
     S.status = status;
     if (stats) *stats = S;
