@@ -164,8 +164,8 @@ class GpuStep:
 
 def launches_per_step(st):
     # init_beta: corr + dtd; solve: atom norms + per round (header reset, LGCD,
-    # 8 refresh kernels); dict_stats: 7; dict_update: 1
-    return 2 + 1 + 10 * int(st["refresh_rounds"]) + 7 + 1
+    # 7 refresh kernels); dict_stats: 7; dict_update: 1
+    return 2 + 1 + 9 * int(st["refresh_rounds"]) + 7 + 1
 
 
 def lgcd_algorithmic_bytes(st, w):

@@ -102,6 +102,13 @@ typedef struct {
     long long deferred;          /* accepted candidates postponed: a neighbour inbox was full */
     long long max_worker_iterations; /* iterations of the busiest worker (critical path)  */
     long long max_worker_updates;    /* updates of the busiest worker                      */
+    long long last_active_wave;  /* latest wave (per worker) that found work             */
+    double t_first_pause_us;     /* latest worker-local time of a first pause             */
+    double t_exit_us;            /* latest worker-local exit time                         */
+    long long wakeups;           /* pauses ended by an incoming message (all workers)     */
+    long long phase_cycles[6];   /* SM cycles summed over workers: wave start, neighbour
+                                    messages, scan + apply, soft-lock tests, end of wave,
+                                    pauses                                                */
     int status;                  /* the returned status                                  */
 } csc_solve_stats;
 

@@ -44,7 +44,9 @@ class SolveStats(C.Structure):
                 ("max_dz_final", C.c_double), ("objective", C.c_double),
                 ("nnz", C.c_longlong), ("kernel_ms", C.c_double), ("deferred", C.c_longlong),
                 ("max_worker_iterations", C.c_longlong), ("max_worker_updates", C.c_longlong),
-                ("status", C.c_int)]
+                ("last_active_wave", C.c_longlong), ("t_first_pause_us", C.c_double),
+                ("t_exit_us", C.c_double), ("wakeups", C.c_longlong),
+                ("phase_cycles", C.c_longlong * 6), ("status", C.c_int)]
 
     def as_dict(self):
         out = {}

@@ -69,7 +69,8 @@ WsLayout plan_workspace(const Geom &g, int max_workers, int rs) {
     L.rr = take((size_t)g.nx() * rs);
     L.phi64 = take((size_t)g.ntab() * sizeof(double));
     L.psi64 = take((size_t)g.nd() * sizeof(double));
-    L.pgd = take(4 * (size_t)g.nd() * sizeof(float));
+    // per-source convolutions of the dictionary step: [cluster rank][K][atoms per CTA x atom]
+    L.pgd = take(2 * ((size_t)g.K * g.nd() + 16 * (size_t)g.natom() * g.K) * sizeof(float));
     L.mbox_slots = take((size_t)max_workers * kDirs * kMailboxCap * sizeof(int4));
     L.mbox_ctl = take((size_t)max_workers * kDirs * 32 * sizeof(int));
     L.total = off;

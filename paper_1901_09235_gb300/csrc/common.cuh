@@ -49,6 +49,8 @@ struct alignas(128) WsHeader {
     int pad5[30];
     long long stat[8];      // updates, iterations, rejected, subtol, messages, deferred
     unsigned long long wmax[2];        // largest per-worker iteration / update counts
+    unsigned long long tmax[4];        // worker timeline (ns after its start): last update, exit, first pause; wake-ups
+    unsigned long long tph[6];         // SM cycles per wave phase, summed over workers
     unsigned long long lmax_bits;      // max |beta| (as bits of a non-negative float/double)
     unsigned long long maxdz_bits;     // max |dZ| on a fresh beta
     long long nnz;          // compacted nonzeros of Z (may exceed the capacity)
@@ -56,7 +58,7 @@ struct alignas(128) WsHeader {
     int status;             // final status of the last solve launch
     double obj_f;           // sum of squared residuals
     double obj_g;           // sum |Z|
-    double pgd_out[4];      // dictionary step: objective, iterations, last step, spare
+    double pgd_out[12];     // dictionary step: objective, iterations, last step, spare, phase cycles [4..9]
     int scan_total;         // deterministic compaction: total count
     int pad6[15];
 };

@@ -225,31 +225,42 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
 }
 
 // ====================================================== PGD + Armijo step
-// Cluster layout: CTA r owns whole atoms [r ka, (r+1) ka), so the
-// projection norms are local.  Its slices of D, the gradient G, the trial
-// point and phi * (trial - D) live in shared memory; the trial difference is
-// published (double-buffered) for the other CTAs, which gather the full
-// difference through distributed shared memory before the convolution.
-// Scalars are combined by publishing per-CTA partials and reading them from
-// every rank after one cluster barrier (double-buffered as well), so one
-// Armijo trial costs two cluster barriers.
+// The data-fit term F(D) = 1/2||X||^2 - <psi, D> + 1/2 <D, phi * D> is
+// quadratic, so a projected step from D with step eta,
+//   D+_k = s_k (D_k - eta G_k),  s_k = 1 / max(1, ||D_k - eta G_k||),
+// moves every atom inside span{D_k, G_k}: D+ - D = sum_k (alpha_k D_k +
+// beta_k G_k) restricted to atom k, alpha_k = s_k - 1, beta_k = -s_k eta.
+// With the per-atom scalars a_k = ||D_k||^2, b_k = <D_k, G_k>, c_k = ||G_k||^2
+// and the K x K matrices M_XY[k][k2] = <X_k, phi * Y_k2> (X, Y in {D, G};
+// M_GD[k][k2] = M_DG[k2][k] because the operator is self-adjoint):
+//   ||D+ - D||^2            = sum_k alpha_k^2 a_k + 2 alpha_k beta_k b_k + beta_k^2 c_k
+//   <D+ - D, phi*(D+ - D)>  = sum_{k,k2} alpha_k alpha_k2 M_DD + alpha_k beta_k2 M_DG
+//                             + beta_k alpha_k2 M_DG[k2][k] + beta_k beta_k2 M_GG.
+// Every Armijo trial (condition <D+ - D, phi * (D+ - D)> eta <= ||D+ - D||^2,
+// the exact form of F(D+) <= F(D) + <G, D+ - D> + ||D+ - D||^2 / (2 eta)
+// for this quadratic F) is therefore O(K^2) scalar work.  One iteration
+// needs a single convolution: with QX_k2 = phi * (X restricted to atom k2)
+// kept per source atom, the accepted step gives G+ = G + sum_k2 (alpha_k2
+// QD_k2 + beta_k2 QG_k2) and QD+_k2 = s_k2 (QD_k2 - eta QG_k2) linearly,
+// and only QG+ is convolved again.
+//
+// Layout: one thread-block cluster, CTA r owns atoms [r ka, (r+1) ka).  Its
+// D and G slices live in shared memory, its per-source convolutions QD/QG in
+// global scratch; the new G and the per-atom scalars / Gram rows are
+// exchanged through distributed shared memory (two cluster barriers per
+// iteration).
 struct PgdArgs {
     const float *phi, *psi;
     float *D;      // in/out
+    float *qd, *qg;  // per-CTA scratch: [cluster rank][K sources][ka * per]
     double *out;   // [objective, iterations, eta]
     double x_sqnorm, tol;
-    int K, P, L0, L1, max_iter, ka, stage_phi;
+    int K, P, L0, L1, max_iter, ka, stage_phi, q_in_smem;
 };
 
 constexpr int kPgdThreads = 1024;
 constexpr int kPgdWarps = kPgdThreads / 32;
-
-struct PgdSmem {
-    float *del;       // full trial difference, K * per (gathered)
-    float *pubdel[2]; // own trial difference, ka * per, double-buffered
-    float *d, *g, *dn, *q;
-    float *phi;       // own rows of phi (optional)
-};
+constexpr int kPgdMaxK = 32;
 
 // Block-wide sum returned to every thread (warp 0 combines the warp sums).
 __device__ __forceinline__ double block_reduce_sum(double v, double *scratch) {
@@ -265,239 +276,361 @@ __device__ __forceinline__ double block_reduce_sum(double v, double *scratch) {
     return scratch[kPgdWarps];
 }
 
-// q[e] = sum_k2 sum_tau2 phi_{k,k2}[tau - tau2] src[k2][p][tau2] for the own
-// entries e = (k, p, ta, tb).  A task is (own row (k, p, ta), four
-// consecutive tb, one source atom k2): it slides a four-wide window of the
-// phi row along tau2 so every step is one broadcast load of src, one load
-// of phi and four FMAs; the K partial sums of an output are combined with
-// shared-memory atomics.
-__device__ __forceinline__ void phi_conv_own(const PgdArgs &a, const PgdSmem &S, int k_lo, int nown,
-                                             const float *src, float *q) {
-    const int LL = a.L0 * a.L1, per = a.P * LL;
-    const int W0 = 2 * a.L0 - 1, W1 = 2 * a.L1 - 1, WW = W0 * W1;
-    for (int e = threadIdx.x; e < nown; e += kPgdThreads) q[e] = 0.f;
+// Three block-wide sums at once, returned to every thread.
+__device__ __forceinline__ void block_reduce3(double &x, double &y, double &z, double (*scr)[kPgdWarps + 1]) {
+    x = warp_sum(x);
+    y = warp_sum(y);
+    z = warp_sum(z);
     __syncthreads();
-    const int nb = (a.L1 + 3) / 4;                 // tb blocks per row
-    const int rows = nown / a.L1;                  // own rows (k, p, ta)
-    const int ntask = rows * nb * a.K;
-    for (int task = threadIdx.x; task < ntask; task += kPgdThreads) {
-        const int k2 = task % a.K;
-        const int rb = task / a.K;
-        const int row = rb / nb, tb0 = (rb % nb) * 4;
-        const int kl = row / (a.P * a.L0), rem = row % (a.P * a.L0), p = rem / a.L0, ta = rem % a.L0;
-        const float *ph = (a.stage_phi ? S.phi + (size_t)kl * a.K * WW
-                                       : a.phi + (size_t)(k_lo + kl) * a.K * WW) + (size_t)k2 * WW;
-        const float *sv = src + (size_t)k2 * per + p * LL;
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-        for (int a2 = 0; a2 < a.L0; a2++) {
-            // phi index along the row: tb - b2 + L1 - 1, for tb = tb0 .. tb0 + 3
-            const float *prow = ph + (ta - a2 + a.L0 - 1) * W1 + tb0 + a.L1 - 1;
-            const float *srow = sv + a2 * a.L1;
-            // f_q holds phi at row index tb0 + q - b2 + L1 - 1; outputs past the
-            // row end (ragged last block) start at zero and are discarded
-            float f0 = prow[0];
-            float f1 = tb0 + 1 < a.L1 ? prow[1] : 0.f;
-            float f2 = tb0 + 2 < a.L1 ? prow[2] : 0.f;
-            float f3 = tb0 + 3 < a.L1 ? prow[3] : 0.f;
-            for (int b2 = 0; b2 < a.L1; b2++) {
-                const float x = srow[b2];
-                acc0 = fmaf(f0, x, acc0);
-                acc1 = fmaf(f1, x, acc1);
-                acc2 = fmaf(f2, x, acc2);
-                acc3 = fmaf(f3, x, acc3);
-                f3 = f2;
-                f2 = f1;
-                f1 = f0;
-                f0 = (b2 + 1 < a.L1) ? prow[-(b2 + 1)] : 0.f;
+    if ((threadIdx.x & 31) == 0) {
+        scr[0][threadIdx.x >> 5] = x;
+        scr[1][threadIdx.x >> 5] = y;
+        scr[2][threadIdx.x >> 5] = z;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const double a0 = warp_sum(scr[0][threadIdx.x]), a1 = warp_sum(scr[1][threadIdx.x]),
+                     a2 = warp_sum(scr[2][threadIdx.x]);
+        if (threadIdx.x == 0) {
+            scr[0][kPgdWarps] = a0;
+            scr[1][kPgdWarps] = a1;
+            scr[2][kPgdWarps] = a2;
+        }
+    }
+    __syncthreads();
+    x = scr[0][kPgdWarps];
+    y = scr[1][kPgdWarps];
+    z = scr[2][kPgdWarps];
+}
+
+// out[k2][e] = sum_tau2 phi_{k,k2}[tau - tau2] src[k2][p][tau2] for the own
+// output entries e = (k, p, tau) and every source atom k2.  Consecutive
+// threads take consecutive tau, so the phi row is read without conflicts and
+// the source value is a broadcast.
+__device__ __forceinline__ void conv_per_source(const PgdArgs &a, const float *sphi, int k_lo, int nown,
+                                                const float *src, float *out) {
+    // work item = (source k2, own row (kl, p, ta), chunk of 32 consecutive tb):
+    // one warp per item, lane = tb; the phi row is read without bank
+    // conflicts and the source value is a broadcast
+    const int LL = a.L0 * a.L1, per = a.P * LL;
+    const int W1 = 2 * a.L1 - 1, WW = (2 * a.L0 - 1) * W1;
+    const int rows = nown / a.L1, chunks = (a.L1 + 31) / 32;
+    const int items = a.K * rows * chunks;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int it = warp; it < items; it += kPgdWarps) {
+        const int k2 = it / (rows * chunks), rem = it % (rows * chunks);
+        const int row = rem / chunks, tb = (rem % chunks) * 32 + lane;
+        const int kl = row / (a.P * a.L0), pr = row % (a.P * a.L0), p = pr / a.L0, ta = pr % a.L0;
+        const float *__restrict__ ph =
+            (a.stage_phi ? sphi + (size_t)kl * a.K * WW : a.phi + (size_t)(k_lo + kl) * a.K * WW) + (size_t)k2 * WW;
+        const float *__restrict__ sv = src + (size_t)k2 * per + p * LL;
+        float acc0 = 0.f, acc1 = 0.f;
+        if (tb < a.L1) {
+            for (int a2 = 0; a2 < a.L0; a2++) {
+                const float *__restrict__ prow = ph + (ta - a2 + a.L0 - 1) * W1 + tb + a.L1 - 1;
+                const float *__restrict__ srow = sv + a2 * a.L1;
+                int b2 = 0;
+                for (; b2 + 1 < a.L1; b2 += 2) {
+                    acc0 = fmaf(prow[-b2], srow[b2], acc0);
+                    acc1 = fmaf(prow[-b2 - 1], srow[b2 + 1], acc1);
+                }
+                if (b2 < a.L1) acc0 = fmaf(prow[-b2], srow[b2], acc0);
+            }
+            out[(size_t)k2 * nown + (size_t)row * a.L1 + tb] = acc0 + acc1;
+        }
+    }
+}
+
+// gall[e] = (rank owning entry e).pub[e - its first entry], for all n
+// entries: every remote load of a thread is issued before any store.
+__device__ __forceinline__ void gather_full(cg::cluster_group &cl, const float *pub, float *gall, int n, int per,
+                                            int ka) {
+    constexpr int U = 8;
+    for (int base = threadIdx.x; base < n; base += U * kPgdThreads) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int e = base + u * kPgdThreads;
+            v[u] = 0.f;
+            if (e < n) {
+                const int r = (e / per) / ka;
+                v[u] = cl.map_shared_rank(pub, (unsigned)r)[e - r * ka * per];
             }
         }
-        float *qo = q + (size_t)row * a.L1 + tb0;
-        atomicAdd(qo, acc0);
-        if (tb0 + 1 < a.L1) atomicAdd(qo + 1, acc1);
-        if (tb0 + 2 < a.L1) atomicAdd(qo + 2, acc2);
-        if (tb0 + 3 < a.L1) atomicAdd(qo + 3, acc3);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int e = base + u * kPgdThreads;
+            if (e < n) gall[e] = v[u];
+        }
     }
 }
 
 __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int LL = a.L0 * a.L1, per = a.P * LL, n = a.K * per;
-    const int W0 = 2 * a.L0 - 1, W1 = 2 * a.L1 - 1, WW = W0 * W1;
+    const int K = a.K, LL = a.L0 * a.L1, per = a.P * LL, n = K * per;
+    const int WW = (2 * a.L0 - 1) * (2 * a.L1 - 1);
     const int rank = (int)cl.block_rank(), ncl = (int)cl.num_blocks();
-    const int k_lo = min(a.K, rank * a.ka), k_hi = min(a.K, k_lo + a.ka);
+    const int k_lo = min(K, rank * a.ka), k_hi = min(K, k_lo + a.ka);
     const int nk = k_hi - k_lo, nown = nk * per, e0 = k_lo * per;
     const int own_cap = a.ka * per;
 
-    PgdSmem S;
-    float *f = reinterpret_cast<float *>(smem_raw);
-    S.del = f;
-    f += n;
-    S.pubdel[0] = f;
-    f += own_cap;
-    S.pubdel[1] = f;
-    f += own_cap;
-    S.d = f;
-    f += own_cap;
-    S.g = f;
-    f += own_cap;
-    S.dn = f;
-    f += own_cap;
-    S.q = f;
-    f += own_cap;
-    S.phi = f;
+    // dynamic shared memory
+    double *sa = reinterpret_cast<double *>(smem_raw), *sb = sa + K, *sc = sb + K;
+    double *pubsc = sc + K;                       // [2][ka][3 + 3K] own scalars and Gram rows
+    const int rowlen = 3 + 3 * K;
+    float *gall = reinterpret_cast<float *>(pubsc + 2 * (size_t)a.ka * rowlen);
+    float *sD = gall + n, *sG = sD + own_cap;
+    float *pubG = sG + own_cap;                   // [2][own_cap]
+    float *sphi = pubG + 2 * (size_t)own_cap;
+    float *qsm = sphi + (a.stage_phi ? (size_t)a.ka * K * WW : 0);
+    float *qd = a.q_in_smem ? qsm : a.qd + (size_t)rank * K * own_cap;
+    float *qg = a.q_in_smem ? qsm + (size_t)K * own_cap : a.qg + (size_t)rank * K * own_cap;
 
-    __shared__ double pub[2][8];
     __shared__ double scratch[kPgdWarps + 1];
-    __shared__ double anrm[16];
-    __shared__ double bcast[4];
-    int pb = 0;
-    // publish up to 4 block totals, one cluster barrier, read the cluster sums
-    auto cluster_sum4 = [&](double v0, double v1, double v2, double v3, double *out4, bool as_max0) {
-        if (threadIdx.x == 0) {
-            pub[pb][0] = v0;
-            pub[pb][1] = v1;
-            pub[pb][2] = v2;
-            pub[pb][3] = v3;
-        }
-        cl.sync();
-        if (threadIdx.x < 32) {
-            double t[4] = {0, 0, 0, 0};
-            if ((int)threadIdx.x < ncl) {
-                const double *rp = cl.map_shared_rank(&pub[pb][0], (unsigned)threadIdx.x);
-                for (int i = 0; i < 4; i++) t[i] = rp[i];
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                double x = __shfl_xor_sync(0xffffffffu, t[0], o);
-                t[0] = as_max0 ? fmax(t[0], x) : t[0] + x;
-                for (int i = 1; i < 4; i++) t[i] += __shfl_xor_sync(0xffffffffu, t[i], o);
-            }
-            if (threadIdx.x == 0)
-                for (int i = 0; i < 4; i++) bcast[i] = t[i];
-        }
-        __syncthreads();
-        for (int i = 0; i < 4; i++) out4[i] = bcast[i];
-        pb ^= 1;
-    };
+    __shared__ double scr3[3][kPgdWarps + 1];
+    __shared__ float s_alpha[kPgdMaxK], s_beta[kPgdMaxK], s_scale[kPgdMaxK];
+    __shared__ float fMDD[kPgdMaxK * kPgdMaxK], fMDG[kPgdMaxK * kPgdMaxK], fMGG[kPgdMaxK * kPgdMaxK];
+    __shared__ double s_ctl[4];  // eta, dsq, dnorm, stop
+    int par = 0;
 
-    // stage own slices, own rows of phi, the full D (for the first gradient)
-    for (int e = threadIdx.x; e < nown; e += kPgdThreads) S.d[e] = a.D[e0 + e];
-    for (int e = threadIdx.x; e < n; e += kPgdThreads) S.del[e] = a.D[e];
+    // stage own slices and phi rows; the full D is the first convolution input
+    for (int e = threadIdx.x; e < nown; e += kPgdThreads) sD[e] = a.D[e0 + e];
+    for (int e = threadIdx.x; e < n; e += kPgdThreads) gall[e] = a.D[e];
     if (a.stage_phi)
-        for (size_t e = threadIdx.x; e < (size_t)nk * a.K * WW; e += kPgdThreads)
-            S.phi[e] = a.phi[(size_t)k_lo * a.K * WW + e];
+        for (size_t e = threadIdx.x; e < (size_t)nk * K * WW; e += kPgdThreads)
+            sphi[e] = a.phi[(size_t)k_lo * K * WW + e];
     __syncthreads();
-
-    // Lipschitz bound max_k sum_k2 sum_d |phi_{k,k2}[d]| over own rows, then cluster max
+    // Lipschitz bound of the gradient: max_k sum_k2 sum_d |phi_{k,k2}[d]|
     double lip_loc = 0.0;
     for (int kl = 0; kl < nk; kl++) {
-        double s = 0.0;
-        for (size_t q = threadIdx.x; q < (size_t)a.K * WW; q += kPgdThreads)
-            s += fabs((double)a.phi[(size_t)(k_lo + kl) * a.K * WW + q]);
-        lip_loc = fmax(lip_loc, block_reduce_sum(s, scratch));
+        double t = 0.0;
+        for (size_t q = threadIdx.x; q < (size_t)K * WW; q += kPgdThreads)
+            t += fabs((double)a.phi[(size_t)(k_lo + kl) * K * WW + q]);
+        lip_loc = fmax(lip_loc, block_reduce_sum(t, scratch));
     }
-    // G = phi * D - psi on the own slice
-    phi_conv_own(a, S, k_lo, nown, S.del, S.q);
+    // QD = phi * D per source; G = sum_k2 QD_k2 - psi
+    conv_per_source(a, sphi, k_lo, nown, gall, qd);
     __syncthreads();
-    for (int e = threadIdx.x; e < nown; e += kPgdThreads) S.g[e] = S.q[e] - a.psi[e0 + e];
-    double tot[4];
-    cluster_sum4(lip_loc, 0, 0, 0, tot, true);
-    const double lip = tot[0];
+    for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
+        float g = -a.psi[e0 + e];
+        for (int k2 = 0; k2 < K; k2++) g += qd[(size_t)k2 * own_cap + e];
+        sG[e] = g;
+        pubG[e] = g;
+    }
+    // publish lip for the cluster max (slot 0 of the scalar rows)
+    if (threadIdx.x == 0) pubsc[0] = lip_loc;
+    cl.sync();
+    double lip = 0.0;
+    for (int r = 0; r < ncl; r++) lip = fmax(lip, cl.map_shared_rank(pubsc, r)[0]);
+    // full G for the first QG convolution
+    gather_full(cl, pubG, gall, n, per, a.ka);
+    __syncthreads();
+
+    // (re)compute QG from gall, then own scalars and Gram rows, then share them
+    unsigned long long ph[6] = {0, 0, 0, 0, 0, 0}, tc = clock64(), tn;
+#define PGD_TICK(i)      \
+    tn = clock64();      \
+    ph[i] += tn - tc;    \
+    tc = tn;
+    auto refresh_stats = [&]() {
+        conv_per_source(a, sphi, k_lo, nown, gall, qg);
+        __syncthreads();
+        PGD_TICK(4)
+        double *mine = pubsc + (size_t)par * a.ka * rowlen;
+        for (int kl = 0; kl < nk; kl++) {
+            const float *d = sD + kl * per, *g = sG + kl * per;
+            float v[3] = {0.f, 0.f, 0.f};
+            for (int e = threadIdx.x; e < per; e += kPgdThreads) {
+                v[0] = fmaf(d[e], d[e], v[0]);
+                v[1] = fmaf(d[e], g[e], v[1]);
+                v[2] = fmaf(g[e], g[e], v[2]);
+            }
+            double r0 = v[0], r1 = v[1], r2 = v[2];
+            block_reduce3(r0, r1, r2, scr3);
+            if (threadIdx.x == 0) {
+                mine[kl * rowlen + 0] = r0;
+                mine[kl * rowlen + 1] = r1;
+                mine[kl * rowlen + 2] = r2;
+            }
+            // Gram rows: warp w takes sources k2 = w, w + 32, ...
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int k2 = warp; k2 < K; k2 += kPgdWarps) {
+                const float *qdr = qd + (size_t)k2 * own_cap + kl * per;
+                const float *qgr = qg + (size_t)k2 * own_cap + kl * per;
+                float dd = 0.f, dg = 0.f, gg = 0.f;
+                for (int e = lane; e < per; e += 32) {
+                    dd = fmaf(d[e], qdr[e], dd);
+                    dg = fmaf(d[e], qgr[e], dg);
+                    gg = fmaf(g[e], qgr[e], gg);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+                    dg += __shfl_xor_sync(0xffffffffu, dg, o);
+                    gg += __shfl_xor_sync(0xffffffffu, gg, o);
+                }
+                if (lane == 0) {
+                    mine[kl * rowlen + 3 + k2] = dd;
+                    mine[kl * rowlen + 3 + K + k2] = dg;
+                    mine[kl * rowlen + 3 + 2 * K + k2] = gg;
+                }
+            }
+        }
+        cl.sync();
+        for (int q = threadIdx.x; q < K * rowlen; q += kPgdThreads) {
+            const int k = q / rowlen, i = q % rowlen;
+            const int r = k / a.ka, kl = k % a.ka;
+            const double v = cl.map_shared_rank(pubsc + (size_t)par * a.ka * rowlen, r)[kl * rowlen + i];
+            if (i == 0) sa[k] = v;
+            else if (i == 1) sb[k] = v;
+            else if (i == 2) sc[k] = v;
+            else if (i < 3 + K) fMDD[k * K + (i - 3)] = (float)v;
+            else if (i < 3 + 2 * K) fMDG[k * K + (i - 3 - K)] = (float)v;
+            else fMGG[k * K + (i - 3 - 2 * K)] = (float)v;
+        }
+        par ^= 1;
+        __syncthreads();
+    };
+    refresh_stats();
 
     double eta = lip > 0.0 ? 1.0 / lip : 0.0;
-    int it = 0, tb = 0;
+    int it = 0;
     if (lip > 0.0) {
         for (it = 0; it < a.max_iter; it++) {
-            if (it > 0) eta *= 2.0;
-            double dsq = 0.0, dnorm = 0.0;
-            for (int bt = 0; bt < 60; bt++) {
-                // trial point, projected atom by atom (norms are local)
-                __syncthreads();
-                for (int e = threadIdx.x; e < nown; e += kPgdThreads) S.dn[e] = S.d[e] - (float)eta * S.g[e];
-                __syncthreads();
-                for (int kl = 0; kl < nk; kl++) {
-                    double s = 0.0;
-                    for (int e = threadIdx.x; e < per; e += kPgdThreads) {
-                        double v = S.dn[kl * per + e];
-                        s += v * v;
+            // Armijo backtracking by warp 0 on the scalars (FP32 terms, FP64 sums)
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                double e_try = it > 0 ? 2.0 * eta : eta, dsq = 0.0, dnorm = 0.0;
+                {
+                    double dn = 0.0;
+                    for (int k = lane; k < K; k += 32) dn += sa[k];
+                    dnorm = warp_sum(dn);
+                }
+                for (int bt = 0; bt < 60; bt++) {
+                    double ds = 0.0;
+                    for (int k = lane; k < K; k += 32) {
+                        // scale 1 / max(1, ||D_k - eta G_k||): FP32 rsqrt refined by
+                        // two Newton steps in FP64 (multiplies only)
+                        const double nn = sa[k] - 2.0 * e_try * sb[k] + e_try * e_try * sc[k];
+                        double sk = 1.0;
+                        if (nn > 1.0) {
+                            double r = (double)rsqrtf((float)nn);
+                            r = r * (1.5 - 0.5 * nn * r * r);
+                            r = r * (1.5 - 0.5 * nn * r * r);
+                            sk = r;
+                        }
+                        const double al = sk - 1.0, be = -sk * e_try;
+                        ds += al * al * sa[k] + 2.0 * al * be * sb[k] + be * be * sc[k];
+                        s_scale[k] = (float)sk;
+                        s_alpha[k] = (float)al;
+                        s_beta[k] = (float)be;
                     }
-                    s = block_reduce_sum(s, scratch);
-                    if (threadIdx.x == 0) anrm[kl] = sqrt(s);
+                    __syncwarp();
+                    float qf = 0.f;
+                    for (int q = lane; q < K * K; q += 32) {
+                        const int k = q / K, k2 = q % K;
+                        const float al = s_alpha[k], be = s_beta[k], al2 = s_alpha[k2], be2 = s_beta[k2];
+                        qf += al * (al2 * fMDD[q] + be2 * fMDG[q]) + be * (al2 * fMDG[k2 * K + k] + be2 * fMGG[q]);
+                    }
+                    for (int o = 16; o > 0; o >>= 1) qf += __shfl_xor_sync(0xffffffffu, qf, o);
+                    dsq = warp_sum(ds);
+                    if ((double)qf * e_try <= dsq || bt == 59) break;
+                    e_try *= 0.5;
+                    __syncwarp();
                 }
-                __syncthreads();
-                double dd = 0.0, d0 = 0.0;
-                float *pd = S.pubdel[tb];
-                for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
-                    double nr = anrm[e / per];
-                    float v = S.dn[e];
-                    if (nr > 1.0) v = (float)((double)v / nr);
-                    S.dn[e] = v;
-                    float dl = v - S.d[e];
-                    pd[e] = dl;
-                    dd += (double)dl * dl;
-                    d0 += (double)S.d[e] * S.d[e];
+                if (lane == 0) {
+                    s_ctl[0] = e_try;
+                    s_ctl[1] = dsq;
+                    s_ctl[2] = dnorm;
+                    s_ctl[3] = sqrt(dsq) < a.tol * sqrt(dnorm) ? 1.0 : 0.0;
                 }
-                dd = block_reduce_sum(dd, scratch);
-                d0 = block_reduce_sum(d0, scratch);
-                cluster_sum4(dd, d0, 0, 0, tot, false);  // also publishes pubdel[tb]
-                dsq = tot[0];
-                dnorm = tot[1];
-                // gather the full difference from every rank
-                for (int r = 0; r < ncl; r++) {
-                    const int rlo = min(a.K, r * a.ka) * per, rhi = min(a.K, r * a.ka + a.ka) * per;
-                    const float *rp = cl.map_shared_rank(S.pubdel[tb], r);
-                    for (int e = threadIdx.x; e < rhi - rlo; e += kPgdThreads) S.del[rlo + e] = rp[e];
-                }
-                __syncthreads();
-                phi_conv_own(a, S, k_lo, nown, S.del, S.q);
-                __syncthreads();
-                double qd = 0.0;
-                for (int e = threadIdx.x; e < nown; e += kPgdThreads) qd += (double)pd[e] * S.q[e];
-                qd = block_reduce_sum(qd, scratch);
-                cluster_sum4(qd, 0, 0, 0, tot, false);
-                tb ^= 1;
-                if (tot[0] * eta <= dsq) break;
-                eta *= 0.5;
             }
-            // accept: D = D+, G = G + phi * (D+ - D)
+            __syncthreads();
+            PGD_TICK(0)
+            eta = s_ctl[0];
+            const float feta = (float)eta;
+            // accept: D+ = D + alpha D + beta G; G+ = G + sum_k2 (alpha QD + beta QG); QD+ linear
+            float *pg = pubG + (size_t)par * own_cap;
             for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
-                S.d[e] = S.dn[e];
-                S.g[e] += S.q[e];
+                const int k = k_lo + e / per;
+                const float d = sD[e], g = sG[e];
+                sD[e] = fmaf(s_beta[k], g, (1.0f + s_alpha[k]) * d);
+                float gn = g;
+                for (int k2 = 0; k2 < K; k2++) {
+                    const size_t o = (size_t)k2 * own_cap + e;
+                    const float qdv = qd[o], qgv = qg[o];
+                    gn = fmaf(s_alpha[k2], qdv, fmaf(s_beta[k2], qgv, gn));
+                    qd[o] = s_scale[k2] * fmaf(-feta, qgv, qdv);
+                }
+                sG[e] = gn;
+                pg[e] = gn;
             }
-            if (sqrt(dsq) < a.tol * sqrt(dnorm)) {
+            const bool stop = s_ctl[3] != 0.0;
+            PGD_TICK(1)
+            if (stop) {
                 it++;
                 break;
             }
+            cl.sync();  // every rank's new G is published
+            PGD_TICK(2)
+            gather_full(cl, pubG + (size_t)par * own_cap, gall, n, per, a.ka);
+            __syncthreads();
+            PGD_TICK(3)
+            refresh_stats();
+            PGD_TICK(5)
         }
     }
     __syncthreads();
     // F(D) = 1/2||X||^2 - 1/2 <psi, D> + 1/2 <D, G>; write D back
-    double pdv = 0.0, dg = 0.0;
+    double pdv = 0.0, dgv = 0.0;
     for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
-        pdv += (double)a.psi[e0 + e] * S.d[e];
-        dg += (double)S.d[e] * S.g[e];
-        a.D[e0 + e] = S.d[e];
+        pdv += (double)a.psi[e0 + e] * sD[e];
+        dgv += (double)sD[e] * sG[e];
+        a.D[e0 + e] = sD[e];
     }
     pdv = block_reduce_sum(pdv, scratch);
-    dg = block_reduce_sum(dg, scratch);
-    cluster_sum4(pdv, dg, 0, 0, tot, false);
+    dgv = block_reduce_sum(dgv, scratch);
+    __shared__ double fin[2];
+    if (threadIdx.x == 0) {
+        fin[0] = pdv;
+        fin[1] = dgv;
+    }
+    cl.sync();
     if (rank == 0 && threadIdx.x == 0) {
-        a.out[0] = 0.5 * a.x_sqnorm - 0.5 * tot[0] + 0.5 * tot[1];
+        double tp = 0.0, tg = 0.0;
+        for (int r = 0; r < ncl; r++) {
+            tp += cl.map_shared_rank(fin, r)[0];
+            tg += cl.map_shared_rank(fin, r)[1];
+        }
+        a.out[0] = 0.5 * a.x_sqnorm - 0.5 * tp + 0.5 * tg;
         a.out[1] = (double)it;
         a.out[2] = eta;
+        for (int i = 0; i < 6; i++) a.out[4 + i] = (double)ph[i];
     }
     cl.sync();  // keep every rank's shared memory alive until all reads are done
+}
+
+static size_t pgd_smem(const Geom &g, int ka, bool stage, bool qsm) {
+    const long long per = (long long)g.P * g.L0 * g.L1, n = g.nd();
+    const int K = g.K, rowlen = 3 + 3 * K;
+    size_t d = (3 * (size_t)K + 2 * (size_t)ka * rowlen) * sizeof(double);
+    size_t f = ((size_t)n + 4 * (size_t)ka * per + (stage ? (size_t)ka * K * g.nw() : 0) +
+                (qsm ? 2 * (size_t)K * ka * per : 0)) *
+               sizeof(float);
+    return d + f;
 }
 
 int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x_sqnorm, float *D,
                      int max_iter, double tol, double *obj_out, int *it_out, unsigned char *ws,
                      const WsLayout &L, cudaStream_t st) {
+    if (g.K > kPgdMaxK) return CSC_ERR_UNIMPLEMENTED;
     WsHeader *h = reinterpret_cast<WsHeader *>(ws + L.hdr);
-    const long long per = (long long)g.P * g.L0 * g.L1, n = g.nd();
     PgdArgs a;
     a.phi = phi;
     a.psi = psi;
     a.D = D;
+    a.qd = reinterpret_cast<float *>(ws + L.pgd);
+    a.qg = a.qd + (size_t)g.K * g.nd() + 16 * (size_t)g.natom() * g.K;
     a.out = h->pgd_out;
     a.x_sqnorm = x_sqnorm;
     a.tol = tol;
@@ -519,27 +652,28 @@ int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x
     // fewest atoms per CTA (largest cluster, at most 16) that fits and can be
     // scheduled; the choice is cached per (device, K, P, L0, L1)
     struct Choice {
-        int dev, K, P, L0, L1, ka, stage;
+        int dev, K, P, L0, L1, ka, stage, qsm;
         size_t smem;
     };
     static thread_local std::vector<Choice> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    const Choice *hit = nullptr;
-    for (const Choice &c : cache)
-        if (c.dev == dev && c.K == g.K && c.P == g.P && c.L0 == g.L0 && c.L1 == g.L1) hit = &c;
-    if (!hit) {
+    int hit = -1;
+    for (size_t i = 0; i < cache.size(); i++) {
+        const Choice &c = cache[i];
+        if (c.dev == dev && c.K == g.K && c.P == g.P && c.L0 == g.L0 && c.L1 == g.L1) hit = (int)i;
+    }
+    if (hit < 0) {
         CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         bool ok = false;
-        Choice ch{dev, g.K, g.P, g.L0, g.L1, 0, 0, 0};
-        for (int ka = (int)ceil_div(g.K, 16); ka <= 16 && !ok; ka++) {
+        Choice ch{dev, g.K, g.P, g.L0, g.L1, 0, 0, 0, 0};
+        for (int ka = (int)ceil_div(g.K, 16); ka <= g.K && !ok; ka++) {
             const int cs = (int)ceil_div(g.K, ka);
-            size_t base = ((size_t)n + 6 * (size_t)ka * per) * sizeof(float);
-            size_t phi_bytes = (size_t)ka * g.K * g.nw() * sizeof(float);
-            if (base > lim) break;
+            if (pgd_smem(g, ka, false, false) > lim) break;
             ch.ka = ka;
-            ch.stage = base + phi_bytes <= lim;
-            ch.smem = base + (ch.stage ? phi_bytes : 0);
+            ch.qsm = pgd_smem(g, ka, false, true) <= lim;
+            ch.stage = pgd_smem(g, ka, true, ch.qsm) <= lim;
+            ch.smem = pgd_smem(g, ka, ch.stage, ch.qsm);
             CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)ch.smem));
             cfg.gridDim = dim3(cs);
@@ -552,14 +686,16 @@ int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x
         }
         if (!ok) return CSC_ERR_UNIMPLEMENTED;
         cache.push_back(ch);
-        hit = &cache.back();
+        hit = (int)cache.size() - 1;
     }
-    a.ka = hit->ka;
-    a.stage_phi = hit->stage;
-    const int cs = (int)ceil_div(g.K, hit->ka);
-    CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hit->smem));
+    const Choice ch = cache[hit];
+    a.ka = ch.ka;
+    a.stage_phi = ch.stage;
+    a.q_in_smem = ch.qsm;
+    const int cs = (int)ceil_div(g.K, ch.ka);
+    CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ch.smem));
     cfg.gridDim = dim3(cs);
-    cfg.dynamicSmemBytes = hit->smem;
+    cfg.dynamicSmemBytes = ch.smem;
     attr[0].val.clusterDim.x = cs;
     CSC_CUDA(cudaLaunchKernelEx(&cfg, pgd_kernel, a));
     if (obj_out || it_out) {

@@ -437,6 +437,8 @@ __device__ void write_back(const LgcdArgs<real> &a, const Tile<real, NT> &t) {
 //   stop     : set by the communication warp when the run must end.
 constexpr int kCompute = 256;
 constexpr int kAsyncThreads = kCompute + 32;
+constexpr int kWarps = kCompute / 32;
+constexpr int kWout = 8;  // border records one warp may emit per wave
 constexpr int kInRing = 128;
 constexpr int kOutRing = 32;
 enum { RESP_WOKEN = 1, RESP_TERMINATE = 2 };
@@ -560,57 +562,72 @@ __device__ __forceinline__ unsigned warp_argmax_key(double a, unsigned key) {
     return a < 0.0 ? 0xffffffffu : key;
 }
 
-// Soft-lock maxima for a border candidate, by one warp: the largest |dZ| of
-// the neighbours' published band inside V(s0), split by owner index.  Loads
-// are issued in batches so a check costs about one memory round trip.
-template <typename real>
-__device__ __forceinline__ void softlock_warp(const LgcdArgs<real> &a, const Tile<real, kCompute> &t, int li0,
-                                              int lj0, int lane, real *m_lo, real *m_hi) {
-    constexpr int B = 8;
-    real lo = real(-1), hi = real(-1);
-    const int gi0 = t.or0 + li0, gj0 = t.oc0 + lj0;
-    const int n = t.K * t.WW;
-    for (int base = 0; base < n; base += 32 * B) {
-        real vb[B], vz[B];
-        int kk[B], side[B];  // side: 0 none, 1 lower-index owner, 2 higher
-#pragma unroll
-        for (int u = 0; u < B; u++) {
-            const int q = base + u * 32 + lane;
-            side[u] = 0;
-            kk[u] = 0;
-            vb[u] = real(0);
-            vz[u] = real(0);
-            if (q < n) {
-                const int k = q / t.WW, r = q % t.WW;
-                const int gi = gi0 + r / a.W1 - (a.L0 - 1), gj = gj0 + r % a.W1 - (a.L1 - 1);
-                const bool inside_dom = gi >= 0 && gi < a.Z0 && gj >= 0 && gj < a.Z1;
-                const bool inside_tile = gi >= t.or0 && gi < t.or0 + t.h && gj >= t.oc0 && gj < t.oc0 + t.wd;
-                if (inside_dom && !inside_tile) {
-                    const size_t g = ((size_t)k * a.Z0 + gi) * a.Z1 + gj;
-                    vb[u] = ld_relaxed(a.beta + g);
-                    vz[u] = ld_relaxed(a.Z + g);
-                    kk[u] = k;
-                    side[u] = ((gi / a.t0) * a.G1 + gj / a.t1) < t.w ? 1 : 2;
-                }
+// One warp applies an accepted update: beta window (Eq. beta_update), Z, the
+// write-through of border entries and, for a border update, the record for
+// the neighbours (needs a free out-ring slot, else the update is deferred).
+template <typename real, int kWarps, int kWout>
+__device__ __forceinline__ void apply_update_warp(const LgcdArgs<real> &a, const Tile<real, kCompute> &t, int k0,
+                                                  int li0, int lj0, real znew, real dz, bool border, int lane,
+                                                  int warp, int par, int &room_left, int (*wout_n)[kWarps],
+                                                  int4 (*wout_rec)[kWarps][kWout],
+                                                  int (*wout_mask)[kWarps][kWout], long long &n_upd,
+                                                  long long &n_def, real guard) {
+    int dl[kDirs];
+    int nd = 0;
+    if (border) {
+        int ok = 0;
+        if (lane == 0) {
+            nd = target_dirs<real, kCompute>(a, t, li0, lj0, dl);
+            if (nd == 0) ok = 1;
+            else if (wout_n[par][warp] < kWout) {
+                ok = atomicSub(&room_left, 1) > 0;
+                if (!ok) atomicAdd(&room_left, 1);
+            }
+            if (!ok) n_def++;
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) return;
+    }
+    const real *__restrict__ row = t.sdtd + (size_t)k0 * t.K * t.WW;
+    real *__restrict__ sb = t.sbeta;
+    for (int r = lane; r < t.WW; r += 32) {
+        const int li = li0 + r / a.W1 - (a.L0 - 1), lj = lj0 + r % a.W1 - (a.L1 - 1);
+        if (li < 0 || li >= t.h || lj < 0 || lj >= t.wd) continue;
+        const bool band = in_band(li, lj, t.h, t.wd, a.L0, a.L1);
+        const int kskip = (li == li0 && lj == lj0) ? k0 : -1;
+        const int base = li * a.t1 + lj;
+        real *gb = a.beta + ((size_t)t.or0 + li) * a.Z1 + t.oc0 + lj;
+        const size_t gstride = (size_t)a.Z0 * a.Z1;
+#pragma unroll 4
+        for (int k = 0; k < t.K; k++) {
+            if (k == kskip) continue;
+            const int idx = base + k * t.TS;
+            const real v = sub_prod(sb[idx], row[k * t.WW + r], dz);
+            sb[idx] = v;
+            if (band) st_relaxed(gb + k * gstride, v);
+        }
+    }
+    if (lane == 0) {
+        t.sz[k0 * t.TS + li0 * a.t1 + lj0] = znew;
+        n_upd++;
+        if (border) {
+            st_relaxed(a.Z + ((size_t)k0 * a.Z0 + t.or0 + li0) * a.Z1 + t.oc0 + lj0, znew);
+            if (nd > 0) {
+                int mask = 0;
+                for (int i = 0; i < nd; i++) mask |= 1 << dl[i];
+                const int o = wout_n[par][warp]++;
+                wout_rec[par][warp][o] = pack_msg(k0, (t.or0 + li0) * a.Z1 + t.oc0 + lj0, dz);
+                wout_mask[par][warp][o] = mask;
             }
         }
-#pragma unroll
-        for (int u = 0; u < B; u++) {
-            if (side[u] == 0) continue;
-            const int k = kk[u];
-            real d = coord_update(vb[u], a.lambda, t.snrm[k], t.sinv[k]) - vz[u];
-            d = d < real(0) ? -d : d;
-            if (side[u] == 1) lo = max(lo, d);
-            else hi = max(hi, d);
+        if (a.max_updates > 0) {
+            unsigned long long prev = atomicAdd(&a.hdr->updates_total, 1ull);
+            if ((long long)prev + 1 >= a.max_updates) set_stop(a.hdr, CSC_NOT_CONVERGED);
         }
+        const real az = znew < real(0) ? -znew : znew;
+        if (a.guard_on && az > guard) set_stop(a.hdr, CSC_ERR_DIVERGED);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    *m_lo = lo;
-    *m_hi = hi;
+    __syncwarp();
 }
 
 template <typename real>
@@ -759,12 +776,23 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
     // Prop. A.2 is zero).  Each wave processes every sub-domain of one colour,
     // one warp per sub-domain; a sweep visits every colour once.
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kWarps = kCompute / 32;
-    constexpr int kWout = 8;  // border records one warp may emit per wave
     __shared__ int wact[2][kWarps], wout_n[2][kWarps], room_left;
     __shared__ int4 wout_rec[2][kWarps][kWout];
     __shared__ int wout_mask[2][kWarps][kWout];
+    constexpr int kPend = 2;  // border candidates one warp may park per wave
+    __shared__ int pend_n[kWarps];
+    __shared__ int pend_pos[kWarps][kPend][3];  // k0, li0, lj0
+    __shared__ real pend_z[kWarps][kPend][2];   // Z', dZ
+    __shared__ unsigned pend_lo[kWarps * kPend], pend_hi[kWarps * kPend];
     long long n_upd = 0, n_it = 0, n_rej = 0, n_sub = 0, n_def = 0, n_wave = 0;
+    __shared__ unsigned long long t_first_idle;
+    long long last_active_wave = 0;
+    __shared__ int n_wake;
+    const unsigned long long t_start = globaltimer_ns();
+    if (tid == 0) {
+        t_first_idle = 0;
+        n_wake = 0;
+    }
     real guard = real(0);
     if (a.guard_on) {
         double g = 1e300;
@@ -780,6 +808,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
         if (ccount[c] > 0) colors[ncol++] = c;
     }
     int ci = 0, quiet = 0;
+    unsigned long long ph[6] = {0, 0, 0, 0, 0, 0}, tc = clock64(), tn;
     for (;;) {
         if (tid == 0) {
             S.nmsg = S.in_head - S.in_tail;
@@ -787,11 +816,15 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
             room_left = kOutRing - (S.out_head - S.out_tail);
         }
         cbar();
+        tn = clock64();
+        ph[0] += tn - tc;
+        tc = tn;
         if (S.bstop) break;
         const int par = (int)(n_wave & 1);
         if (lane == 0) {
             wact[par][warp] = 0;
             wout_n[par][warp] = 0;
+            pend_n[warp] = 0;
         }
         const int nmsg = S.nmsg;
         if (nmsg > 0) {
@@ -818,6 +851,9 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
             cbar();
             if (tid == 0) S.in_tail = base + nmsg;
         }
+        tn = clock64();
+        ph[1] += tn - tc;
+        tc = tn;
         // ---- one wave: the sub-domains of colour c, one warp each
         const int c = colors[ci];
         const int rc = c >> 1, cc = c & 1, ncc = (ns1 - cc + 1) / 2;
@@ -828,13 +864,17 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
             // candidate scan (Eq. gcd_candidate) with the oracle's tie-break
             real ba = real(-1);
             unsigned bkey = 0xffffffffu;
+            const real *__restrict__ sbr = t.sbeta;
+            const real *__restrict__ szr = t.sz;
             for (int r = lane; r < nb; r += 32) {
                 const int li = r0 + r / bw, lj = c0 + r % bw;
                 const unsigned pos = (unsigned)(li * a.t1 + lj) * (unsigned)t.K;
-                int idx = li * a.t1 + lj;
-                for (int k = 0; k < t.K; k++, idx += t.TS) {
-                    const real zn = coord_update(t.sbeta[idx], a.lambda, t.snrm[k], t.sinv[k]);
-                    real d = zn - t.sz[idx];
+                const int base = li * a.t1 + lj;
+#pragma unroll 4
+                for (int k = 0; k < t.K; k++) {
+                    const int idx = base + k * t.TS;
+                    const real zn = coord_update(sbr[idx], a.lambda, t.snrm[k], t.sinv[k]);
+                    real d = zn - szr[idx];
                     d = d < real(0) ? -d : d;
                     const unsigned key = pos + (unsigned)k;
                     if (d > ba || (d == ba && key < bkey)) {
@@ -859,90 +899,140 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
             }
             if (lane == 0) wact[par][warp] = 1;
             const bool border = in_band(li0, lj0, t.h, t.wd, a.L0, a.L1);
-            bool accept = true;
-            if (border) {
-                if (a.mode == CSC_MODE_ASYNC) {
-                    real lo, hi;
-                    softlock_warp(a, t, li0, lj0, lane, &lo, &hi);
-                    accept = adz > lo && adz >= hi;
-                    n_rej += (lane == 0 && !accept);
-                }
-                if (accept) {
-                    int ok = 0;
-                    if (lane == 0 && wout_n[par][warp] < kWout) {
-                        ok = atomicSub(&room_left, 1) > 0;
-                        if (!ok) atomicAdd(&room_left, 1);
-                    }
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (!ok) {
-                        accept = false;
-                        n_def += (lane == 0);
-                    }
-                }
-            }
-            if (!accept) continue;
-            // beta_k[s] -= C[k][k0][s - s0] dz over V(s0) in the tile (Eq. beta_update)
-            const real *row = t.sdtd + (size_t)k0 * t.K * t.WW;
-            for (int r = lane; r < t.WW; r += 32) {
-                const int li = li0 + r / a.W1 - (a.L0 - 1), lj = lj0 + r % a.W1 - (a.L1 - 1);
-                if (li < 0 || li >= t.h || lj < 0 || lj >= t.wd) continue;
-                const bool band = in_band(li, lj, t.h, t.wd, a.L0, a.L1);
-                const bool center = li == li0 && lj == lj0;
-                int idx = li * a.t1 + lj;
-                for (int k = 0; k < t.K; k++, idx += t.TS) {
-                    if (center && k == k0) continue;
-                    const real v = sub_prod(t.sbeta[idx], row[k * t.WW + r], dz);
-                    t.sbeta[idx] = v;
-                    if (band) st_relaxed(a.beta + ((size_t)k * a.Z0 + t.or0 + li) * a.Z1 + t.oc0 + lj, v);
-                }
-            }
-            __syncwarp();
-            if (lane == 0) {
-                t.sz[idx0] = znew;
-                n_upd++;
-                if (border) {
-                    st_relaxed(a.Z + ((size_t)k0 * a.Z0 + t.or0 + li0) * a.Z1 + t.oc0 + lj0, znew);
-                    int dl[kDirs];
-                    const int nd = target_dirs<real, kCompute>(a, t, li0, lj0, dl);
-                    if (nd > 0) {
-                        int mask = 0;
-                        for (int i = 0; i < nd; i++) mask |= 1 << dl[i];
-                        const int o = wout_n[par][warp]++;
-                        wout_rec[par][warp][o] = pack_msg(k0, (t.or0 + li0) * a.Z1 + t.oc0 + lj0, dz);
-                        wout_mask[par][warp][o] = mask;
+            if (border && a.mode == CSC_MODE_ASYNC) {
+                // park it: the soft-lock test runs for all parked candidates at once
+                if (lane == 0) {
+                    const int o = pend_n[warp];
+                    if (o < kPend) {
+                        pend_pos[warp][o][0] = k0;
+                        pend_pos[warp][o][1] = li0;
+                        pend_pos[warp][o][2] = lj0;
+                        pend_z[warp][o][0] = znew;
+                        pend_z[warp][o][1] = dz;
+                        pend_lo[warp * kPend + o] = 0u;
+                        pend_hi[warp * kPend + o] = 0u;
+                        pend_n[warp] = o + 1;
                     } else {
-                        atomicAdd(&room_left, 1);  // reserved slot not needed
+                        n_def++;
                     }
                 }
-                if (a.max_updates > 0) {
-                    unsigned long long prev = atomicAdd(&a.hdr->updates_total, 1ull);
-                    if ((long long)prev + 1 >= a.max_updates) set_stop(a.hdr, CSC_NOT_CONVERGED);
-                }
-                const real az = znew < real(0) ? -znew : znew;
-                if (a.guard_on && az > guard) set_stop(a.hdr, CSC_ERR_DIVERGED);
+                __syncwarp();
+                continue;
             }
-            __syncwarp();
+            apply_update_warp(a, t, k0, li0, lj0, znew, dz, border, lane, warp, par, room_left, wout_n,
+                              wout_rec, wout_mask, n_upd, n_def, guard);
         }
         cbar();
+        tn = clock64();
+        ph[2] += tn - tc;
+        tc = tn;
+        // ---- soft-lock test of the parked border candidates (Eq. soft_lock),
+        // all compute threads together: one batch of loads per thread
+        int ncand = 0;
+        for (int w = 0; w < kWarps; w++) ncand += pend_n[w];
+        if (ncand > 0) {
+            // candidate c's K x window entries are split over the compute
+            // threads; each warp reduces its maxima before one shared atomic
+            const int per = t.K * t.WW;
+            constexpr int B = 8;
+            for (int c = 0; c < ncand; c++) {
+                int slot = -1, rem = c;
+                for (int w = 0; w < kWarps; w++) {
+                    if (rem < pend_n[w]) {
+                        slot = w * kPend + rem;
+                        break;
+                    }
+                    rem -= pend_n[w];
+                }
+                const int *pp = pend_pos[slot / kPend][slot % kPend];
+                const int gi0 = t.or0 + pp[1] - (a.L0 - 1), gj0 = t.oc0 + pp[2] - (a.L1 - 1);
+                unsigned lo = 0u, hi = 0u;
+                for (int base = tid; base < per; base += B * kCompute) {
+                    real vb[B], vz[B];
+                    int kk[B], side[B];
+#pragma unroll
+                    for (int u = 0; u < B; u++) {
+                        const int q = base + u * kCompute;
+                        side[u] = 0;
+                        kk[u] = 0;
+                        vb[u] = real(0);
+                        vz[u] = real(0);
+                        if (q < per) {
+                            const int k = q / t.WW, r = q % t.WW;
+                            const int gi = gi0 + r / a.W1, gj = gj0 + r % a.W1;
+                            const bool in_dom = gi >= 0 && gi < a.Z0 && gj >= 0 && gj < a.Z1;
+                            const bool in_tile = gi >= t.or0 && gi < t.or0 + t.h && gj >= t.oc0 && gj < t.oc0 + t.wd;
+                            if (in_dom && !in_tile) {
+                                const size_t g = ((size_t)k * a.Z0 + gi) * a.Z1 + gj;
+                                vb[u] = ld_relaxed(a.beta + g);
+                                vz[u] = ld_relaxed(a.Z + g);
+                                kk[u] = k;
+                                side[u] = ((gi / a.t0) * a.G1 + gj / a.t1) < t.w ? 1 : 2;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < B; u++) {
+                        if (side[u] == 0) continue;
+                        real d = coord_update(vb[u], a.lambda, t.snrm[kk[u]], t.sinv[kk[u]]) - vz[u];
+                        d = d < real(0) ? -d : d;
+                        const unsigned bits = (unsigned)nonneg_bits((float)d) + 1u;
+                        if (side[u] == 1) lo = max(lo, bits);
+                        else hi = max(hi, bits);
+                    }
+                }
+                lo = __reduce_max_sync(0xffffffffu, lo);
+                hi = __reduce_max_sync(0xffffffffu, hi);
+                if (lane == 0) {
+                    if (lo) atomicMax(&pend_lo[slot], lo);
+                    if (hi) atomicMax(&pend_hi[slot], hi);
+                }
+            }
+            cbar();
+            for (int o = 0; o < pend_n[warp]; o++) {
+                const int slot = warp * kPend + o;
+                const int k0 = pend_pos[warp][o][0], li0 = pend_pos[warp][o][1], lj0 = pend_pos[warp][o][2];
+                const real znew = pend_z[warp][o][0], dz = pend_z[warp][o][1];
+                const real adz = dz < real(0) ? -dz : dz;
+                // compare in the same float encoding the maxima were taken in
+                const unsigned mine = (unsigned)nonneg_bits((float)adz) + 1u;
+                const bool accept = mine > pend_lo[slot] && mine >= pend_hi[slot];
+                if (!accept) {
+                    n_rej += (lane == 0);
+                    continue;
+                }
+                apply_update_warp(a, t, k0, li0, lj0, znew, dz, true, lane, warp, par, room_left, wout_n,
+                                  wout_rec, wout_mask, n_upd, n_def, guard);
+            }
+        }
+        cbar();
+        tn = clock64();
+        ph[3] += tn - tc;
+        tc = tn;
         // ---- end of wave: hand border updates to the communication warp
         bool any = nmsg > 0;
         for (int w = 0; w < kWarps; w++) any |= wact[par][w] != 0;
         if (tid == 0) {
-            int oh = S.out_head;
+            const int oh0 = S.out_head;
+            int oh = oh0;
             for (int w = 0; w < kWarps; w++)
                 for (int i = 0; i < wout_n[par][w]; i++, oh++) {
                     S.out_rec[oh & (kOutRing - 1)] = wout_rec[par][w][i];
                     S.out_mask[oh & (kOutRing - 1)] = wout_mask[par][w][i];
                 }
-            __threadfence_block();
-            S.out_head = oh;
+            if (oh != oh0) {
+                __threadfence_block();
+                S.out_head = oh;
+            }
         }
         n_wave++;
         ci = ci + 1 == ncol ? 0 : ci + 1;
         quiet = any ? 0 : quiet + 1;
+        if (any) last_active_wave = n_wave;
         if (quiet >= ncol) {
             // a full sweep without work: pause (Alg. 3)
             if (tid == 0) {
+                if (t_first_idle == 0) t_first_idle = globaltimer_ns();
                 const int seq = S.idle_seq + 1;
                 __threadfence_block();
                 S.idle_seq = seq;
@@ -956,11 +1046,18 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
                     __nanosleep(64);
                 }
                 S.idle_res = (S.resp_kind == RESP_TERMINATE) || S.stop;
+                n_wake += !S.idle_res;
             }
             cbar();
             if (S.idle_res) break;
             quiet = 0;
+            tn = clock64();
+            ph[5] += tn - tc;
+            tc = tn;
         }
+        tn = clock64();
+        ph[4] += tn - tc;
+        tc = tn;
     }
     // wait for the communication warp to finish before the tile is written
     if (tid == 0) {
@@ -992,6 +1089,11 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
     if (tid == 0) {
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_MESSAGES], (unsigned long long)S.n_msg_sent);
         atomicMax(&a.hdr->wmax[0], (unsigned long long)n_wave);
+        atomicMax(&a.hdr->tmax[0], (unsigned long long)last_active_wave);
+        atomicMax(&a.hdr->tmax[1], globaltimer_ns() - t_start);
+        if (t_first_idle) atomicMax(&a.hdr->tmax[2], t_first_idle - t_start);
+        atomicAdd(&a.hdr->tmax[3], (unsigned long long)n_wake);
+        for (int i = 0; i < 6; i++) atomicAdd(&a.hdr->tph[i], ph[i]);
     }
 }
 
@@ -1148,6 +1250,8 @@ __global__ void reset_header_kernel(WsHeader *h, int workers) {
     h->updates_total = 0;
     for (int i = 0; i < 8; i++) h->stat[i] = 0;
     h->wmax[0] = h->wmax[1] = 0;
+    for (int i = 0; i < 4; i++) h->tmax[i] = 0;
+    for (int i = 0; i < 6; i++) h->tph[i] = 0;
     h->maxdz_bits = 0;
     h->obj_f = 0.0;
     h->obj_g = 0.0;
@@ -1410,6 +1514,11 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
         S.deferred += hh.stat[ST_DEFERRED];
         S.max_worker_iterations = std::max<long long>(S.max_worker_iterations, (long long)hh.wmax[0]);
         S.max_worker_updates = std::max<long long>(S.max_worker_updates, (long long)hh.wmax[1]);
+        S.last_active_wave = std::max(S.last_active_wave, (long long)hh.tmax[0]);
+        S.t_exit_us = std::max(S.t_exit_us, hh.tmax[1] * 1e-3);
+        S.t_first_pause_us = std::max(S.t_first_pause_us, hh.tmax[2] * 1e-3);
+        S.wakeups += (long long)hh.tmax[3];
+        for (int i = 0; i < 6; i++) S.phase_cycles[i] += (long long)hh.tph[i];
         status = hh.stop;
         double maxdz;
         if (sizeof(real) == 4) {

@@ -11,19 +11,22 @@
 namespace csc {
 
 // Nonzeros of Z into (k, s, z) lists; order is unspecified (one atomic per
-// warp).  Counts past the capacity only set the overflow flag.
+// warp).  Counts past the capacity only set the overflow flag.  The same
+// pass accumulates ||Z||_1 in FP64.
 template <typename real, int NT>
 __global__ void __launch_bounds__(NT) compact_any_kernel(const real *Z, long long zpos, int K,
                                                          int *nk, int *ns, real *nzv, long long cap,
                                                          WsHeader *h) {
     const long long n = (long long)K * zpos;
     const int lane = threadIdx.x & 31;
+    double l1 = 0.0;
     for (long long base = (long long)blockIdx.x * NT; base < n; base += (long long)gridDim.x * NT) {
         long long i = base + threadIdx.x;
         real v = i < n ? Z[i] : real(0);
         bool nzb = v != real(0);
         unsigned ball = __ballot_sync(0xffffffffu, nzb);
         if (ball == 0) continue;
+        if (nzb) l1 += fabs((double)v);
         unsigned long long wbase = 0;
         if (lane == 0) wbase = atomicAdd((unsigned long long *)&h->nnz, (unsigned long long)__popc(ball));
         wbase = __shfl_sync(0xffffffffu, wbase, 0);
@@ -38,6 +41,7 @@ __global__ void __launch_bounds__(NT) compact_any_kernel(const real *Z, long lon
             }
         }
     }
+    block_sum_atomic<NT>(l1, &h->obj_g);
 }
 
 template <typename real>
@@ -103,18 +107,10 @@ __global__ void __launch_bounds__(NT) residual_finish_kernel(const double *R, re
                                                              double *out) {
     double s = 0.0;
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
-        double r = R[i];
+        const double r = R[i];
         s += r * r;
         if (Rr) Rr[i] = (real)r;
     }
-    block_sum_atomic<NT>(s, out);
-}
-
-template <typename real, int NT>
-__global__ void __launch_bounds__(NT) l1_kernel(const real *Z, long long n, double *out) {
-    double s = 0.0;
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
-        s += fabs((double)Z[i]);
     block_sum_atomic<NT>(s, out);
 }
 
@@ -153,7 +149,6 @@ int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const re
                                                                 g.L0, g.L1, g.Z0, g.Z1);
     residual_finish_kernel<real, 256><<<grid_for(nx, 256), 256, 0, st>>>(R, beta ? Rr : nullptr, nx,
                                                                          &h->obj_f);
-    l1_kernel<real, 256><<<grid_for(nz, 256), 256, 0, st>>>(Z, nz, &h->obj_g);
     CSC_CUDA(cudaGetLastError());
     if (beta) return launch_corr_refresh<real>(g, Rr, D, Z, nrm, lambda, beta, &h->maxdz_bits, st);
     return CSC_OK;
