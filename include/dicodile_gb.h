@@ -190,6 +190,29 @@ CSC_API int csc_lgcd_solve_f64(const csc_shape *shape, const double *X, const do
                        const csc_solve_opts *opts, void *workspace, size_t workspace_bytes,
                        csc_solve_stats *stats, csc_stream_t stream);
 
+/* cdl_dict_stats for callers that cannot allocate device memory.  The paper
+ * has no counterpart to this call; it exists for embedders that cannot give
+ * the library a workspace at the time they need the statistics -- for example
+ * a plugin inside an application that owns every device allocation, or a
+ * service that reserves all of its device memory at start-up and allocates
+ * nothing afterwards.
+ *   Same arguments, layouts and results as cdl_dict_stats, without the
+ *   workspace: the scratch is a fixed array of CSC_NOALLOC_SCRATCH_BYTES that
+ *   the library keeps on every GPU that loads it until the process exits.
+ *   The call allocates nothing (no cudaMalloc/cudaFree, no allocating library
+ *   routine).
+ *   Returns CSC_ERR_WORKSPACE when the problem needs more scratch than the
+ *   array holds (the nonzero list of Z plus the FP64 accumulators of phi and
+ *   psi; the 1-D P=5, T=200,000, K=10, L=64 problem needs about 1.7 MB).
+ *   The first call on a device looks up the array's device address; make that
+ *   first call before any stream capture.  All calls share the one array:
+ *   calls whose work overlaps on the GPU (different streams, different host
+ *   threads) race and must be serialised by the caller.  Like cdl_dict_stats,
+ *   it synchronises `stream` once to check the nonzero count. */
+#define CSC_NOALLOC_SCRATCH_BYTES (8u << 20)
+CSC_API int cdl_dict_stats_noalloc(const csc_shape *shape, const float *Z, const float *X, float *phi,
+                                   float *psi, csc_stream_t stream);
+
 /* Human-readable name of a status code (static storage). */
 CSC_API const char *csc_status_string(int status);
 

@@ -310,3 +310,25 @@ class Problem:
         p.phi = torch.empty(tab_shape(s), dtype=torch.float32, device=X.device)
         p.psi = torch.empty(tuple(D.shape), dtype=torch.float32, device=X.device)
         return p
+
+
+def cdl_dict_stats_noalloc(Z, X, D_shape, phi=None, psi=None, stream=None):
+    """phi and psi like cdl_dict_stats, for callers that cannot allocate device
+    memory: the library's built-in scratch array is used instead of a caller
+    workspace (the output tensors are still the caller's).  Calls that overlap
+    on the GPU must be serialised by the caller."""
+    import torch
+    _need(Z, torch.float32, "Z")
+    _need(X, torch.float32, "X")
+    lib = load()
+    fn = lib.cdl_dict_stats_noalloc
+    fn.restype = C.c_int
+    fn.argtypes = [C.POINTER(Shape), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    s = make_shape(tuple(X.shape), tuple(D_shape))
+    if phi is None:
+        phi = torch.empty(tab_shape(s), dtype=torch.float32, device=X.device)
+    if psi is None:
+        psi = torch.empty(tuple(D_shape), dtype=torch.float32, device=X.device)
+    _check(fn(C.byref(s), _ptr(Z), _ptr(X), _ptr(phi), _ptr(psi), _stream(stream)),
+           "cdl_dict_stats_noalloc")
+    return phi, psi
