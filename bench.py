@@ -179,6 +179,23 @@ def lgcd_algorithmic_bytes(st, w):
     return st["iterations"] * 8 * K * sub + st["updates"] * (12 * K * win + 4)
 
 
+def lgcd_traffic_per_launch():
+    """DRAM bytes per LGCD launch from the committed ncu summary, or None when
+    the kernel sources changed since those counters were taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "lgcd_async_kernel_csc1d_T200000_P5_K10_L64.md")
+    src = [os.path.join(ROOT, "paper_1901_09235_gb300", "csrc", f) for f in ("lgcd.cu", "common.cuh")]
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()
+    except OSError:
+        return None
+    vals = dict(line.split(" = ", 1) for line in text.splitlines() if " = " in line)
+    if vals.get("source_sha256", "").strip() != h:
+        return None
+    return int(vals["dram_bytes_per_launch"])
+
+
 def smem_peak_gbs(sm_mhz=2070.0, sms=152):
     """Shared-memory bandwidth: 128 B per clock per SM (32 banks x 4 B)."""
     return sms * 128 * sm_mhz * 1e6 / 1e9
@@ -352,7 +369,7 @@ def main():
                                               "max_worker_iterations", "max_worker_updates",
                                               "kernel_ms", "dict_iters")},
         "roofline": {"bound": "smem", "kernel": "lgcd_async_kernel", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": lgcd_traffic_per_launch(),
                      "peak_source": "derived: 152 SMs x 128 B/clk x 2070 MHz (shared memory)",
                      "algorithmic_bytes_per_launch": abytes / len(stats)},
         "e2e": {"value": world * args.steps / tot_e2e, "unit": UNIT,
