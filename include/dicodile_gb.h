@@ -83,6 +83,8 @@ typedef struct {
     int beta_refresh;     /* re-solves allowed after recomputing beta from scratch (>= 0)  */
     int divergence_guard; /* 1 = stop with CSC_ERR_DIVERGED when the Section 5.1 bound hits */
     int warm_start;       /* 1 = Z and beta on entry are a consistent starting point        */
+    int placement;        /* 0 = automatic, 1 = tiles in shared memory, 2 = tiles in global
+                             memory (used when a tile's beta, Z and table do not fit)      */
 } csc_solve_opts;
 
 typedef struct {
@@ -93,6 +95,7 @@ typedef struct {
     long long messages;          /* neighbour notifications (k0, s0, dZ) sent            */
     long long refresh_rounds;    /* beta recomputations from scratch                     */
     int workers;                 /* tiles (one CTA each)                                 */
+    int placement;               /* 1 = shared-memory tiles, 2 = global-memory tiles     */
     int tiles[2];                /* tile grid                                            */
     int tile_size[2];            /* full tile size                                       */
     double max_dz_final;         /* max |dZ| on a freshly recomputed beta (final KKT)    */

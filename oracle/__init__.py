@@ -58,6 +58,9 @@ def _load():
             "orc_dict_grad": (None, [i, i, i, i, p, p, p, p]),
             "orc_dict_objective": (d, [i, i, i, i, p, p, d, p]),
             "orc_pgd_armijo": (i, [i, i, i, i, p, p, d, p, i, d, p]),
+            "orc_beta_at": (None, [i, i, i, i, i, i, p, p, ll, p, p, p]),
+            "orc_beta_from_Z_at": (None, [i, i, i, i, i, i, p, p, p, ll, p, p, p]),
+            "orc_objective_sparse": (d, [i, i, i, i, i, i, p, p, p, d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -239,3 +242,34 @@ def pgd_armijo(phi, psi, x_sqnorm: float, D, max_iter: int = 50, tol: float = 1e
     it = _load().orc_pgd_armijo(*_dict_geom(D), _ptr(phi), _ptr(psi), float(x_sqnorm),
                                 _ptr(D), int(max_iter), float(tol), C.byref(f))
     return D, float(f.value), int(it)
+
+
+def _coords(ks, ss):
+    ks = np.ascontiguousarray(np.asarray(ks, dtype=np.int32))
+    ss = np.ascontiguousarray(np.asarray(ss, dtype=np.int64))
+    assert ks.shape == ss.shape
+    return ks, ss
+
+
+def beta_at(X, D, ks, ss):
+    """beta_k[s] of the initialisation at listed (k, row-major s)."""
+    X, D = _f64(X), _f64(D)
+    ks, ss = _coords(ks, ss)
+    out = np.zeros(len(ks))
+    _load().orc_beta_at(*_geom(X, D), _ptr(X), _ptr(D), len(ks), _ptr(ks), _ptr(ss), _ptr(out))
+    return out
+
+
+def beta_from_Z_at(X, D, Z, ks, ss):
+    """beta from its definition for the current Z at listed (k, s)."""
+    X, D, Z = _f64(X), _f64(D), _f64(Z)
+    ks, ss = _coords(ks, ss)
+    out = np.zeros(len(ks))
+    _load().orc_beta_from_Z_at(*_geom(X, D), _ptr(X), _ptr(D), _ptr(Z), len(ks), _ptr(ks),
+                               _ptr(ss), _ptr(out))
+    return out
+
+
+def objective_sparse(X, D, Z, lam: float) -> float:
+    X, D, Z = _f64(X), _f64(D), _f64(Z)
+    return float(_load().orc_objective_sparse(*_geom(X, D), _ptr(X), _ptr(D), _ptr(Z), float(lam)))

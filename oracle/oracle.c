@@ -510,3 +510,84 @@ int orc_pgd_armijo(int P, int K, int L0, int L1, const double *phi, const double
     if (f_out) *f_out = f;
     return it;
 }
+
+/* ---------------------------------------------------------------------------
+ * Single outputs, for checks on problems too large for the full routines.
+ * ------------------------------------------------------------------------ */
+
+/* beta_k[s] = sum_p sum_tau D_kp[tau] X_p[s + tau] at n listed (k, s), s a
+ * row-major index of the activation domain (Alg. 1 initialisation). */
+void orc_beta_at(int P, int K, int T0, int T1, int L0, int L1, const double *X, const double *D,
+                 long long n, const int *ks, const long long *ss, double *out)
+{
+    int Z1 = T1 - L1 + 1;
+    for (long long q = 0; q < n; q++) {
+        int k = ks[q], i = (int)(ss[q] / Z1), j = (int)(ss[q] % Z1);
+        double acc = 0.0;
+        for (int p = 0; p < P; p++)
+            for (int a = 0; a < L0; a++)
+                for (int b = 0; b < L1; b++)
+                    acc += D[IDX4(k, p, a, b, P, L0, L1)] * X[IDX3(p, i + a, j + b, T0, T1)];
+        out[q] = acc;
+    }
+    (void)K;
+}
+
+/* beta from its definition (Section 3) at n listed (k, s):
+ * sum_p sum_tau D_kp[tau] (X - Z*D)_p[s+tau] + ||D_k||^2 Z_k[s], with the
+ * residual evaluated only where it is needed. */
+void orc_beta_from_Z_at(int P, int K, int T0, int T1, int L0, int L1, const double *X,
+                        const double *D, const double *Z, long long n, const int *ks,
+                        const long long *ss, double *out)
+{
+    int Z0 = T0 - L0 + 1, Z1 = T1 - L1 + 1;
+    for (long long q = 0; q < n; q++) {
+        int k = ks[q], i = (int)(ss[q] / Z1), j = (int)(ss[q] % Z1);
+        double acc = 0.0, nrm = 0.0;
+        for (int p = 0; p < P; p++)
+            for (int a = 0; a < L0; a++)
+                for (int b = 0; b < L1; b++) {
+                    int t0 = i + a, t1 = j + b;
+                    double rec = 0.0; /* (Z*D)_p[t] */
+                    for (int k2 = 0; k2 < K; k2++)
+                        for (int a2 = 0; a2 < L0; a2++)
+                            for (int b2 = 0; b2 < L1; b2++) {
+                                int s0 = t0 - a2, s1 = t1 - b2;
+                                if (s0 < 0 || s0 >= Z0 || s1 < 0 || s1 >= Z1) continue;
+                                double z = Z[IDX3(k2, s0, s1, Z0, Z1)];
+                                if (z != 0.0) rec += z * D[IDX4(k2, p, a2, b2, P, L0, L1)];
+                            }
+                    double d = D[IDX4(k, p, a, b, P, L0, L1)];
+                    acc += d * (X[IDX3(p, t0, t1, T0, T1)] - rec);
+                    nrm += d * d;
+                }
+        out[q] = acc + nrm * Z[IDX3(k, i, j, Z0, Z1)];
+    }
+}
+
+/* 1/2 ||X - Z * D||^2 + lambda ||Z||_1 (Eq. csc) with the reconstruction
+ * accumulated from the nonzeros of Z (zero terms skipped). */
+double orc_objective_sparse(int P, int K, int T0, int T1, int L0, int L1, const double *X,
+                            const double *D, const double *Z, double lambda)
+{
+    int Z0 = T0 - L0 + 1, Z1 = T1 - L1 + 1;
+    size_t nx = (size_t)P * T0 * T1;
+    double *res = malloc(nx * sizeof(double));
+    memcpy(res, X, nx * sizeof(double));
+    double g = 0.0;
+    for (int k = 0; k < K; k++)
+        for (int i = 0; i < Z0; i++)
+            for (int j = 0; j < Z1; j++) {
+                double z = Z[IDX3(k, i, j, Z0, Z1)];
+                if (z == 0.0) continue;
+                g += fabs(z);
+                for (int p = 0; p < P; p++)
+                    for (int a = 0; a < L0; a++)
+                        for (int b = 0; b < L1; b++)
+                            res[IDX3(p, i + a, j + b, T0, T1)] -= z * D[IDX4(k, p, a, b, P, L0, L1)];
+            }
+    double f = 0.0;
+    for (size_t q = 0; q < nx; q++) f += res[q] * res[q];
+    free(res);
+    return 0.5 * f + lambda * g;
+}

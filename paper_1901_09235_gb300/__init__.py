@@ -33,14 +33,15 @@ class SolveOpts(C.Structure):
     _fields_ = [("tile", C.c_int * 2), ("sub", C.c_int * 2), ("mode", C.c_int),
                 ("max_workers", C.c_int), ("max_updates", C.c_longlong),
                 ("timeout_s", C.c_double), ("beta_refresh", C.c_int),
-                ("divergence_guard", C.c_int), ("warm_start", C.c_int)]
+                ("divergence_guard", C.c_int), ("warm_start", C.c_int), ("placement", C.c_int)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("updates", C.c_longlong), ("iterations", C.c_longlong),
                 ("rejected_softlock", C.c_longlong), ("skipped_subtol", C.c_longlong),
                 ("messages", C.c_longlong), ("refresh_rounds", C.c_longlong),
-                ("workers", C.c_int), ("tiles", C.c_int * 2), ("tile_size", C.c_int * 2),
+                ("workers", C.c_int), ("placement", C.c_int), ("tiles", C.c_int * 2),
+                ("tile_size", C.c_int * 2),
                 ("max_dz_final", C.c_double), ("objective", C.c_double),
                 ("nnz", C.c_longlong), ("kernel_ms", C.c_double), ("deferred", C.c_longlong),
                 ("max_worker_iterations", C.c_longlong), ("max_worker_updates", C.c_longlong),

@@ -193,3 +193,26 @@ def test_dict_update(pkg, orc, w):
     assert abs(f_gpu - f_ref) <= 1e-5 * abs(f0 - f_ref) + 1e-7 * abs(f_ref)
     nr = np.sqrt((Dg.reshape(w.K, -1).astype(np.float64) ** 2).sum(1))
     assert np.all(nr <= 1 + 1e-6)
+
+
+@pytest.mark.parametrize("w", ASYNC, ids=[w.name for w in ASYNC])
+def test_async_global_tiles_match_oracle(pkg, orc, w):
+    """The global-memory variant (beta, Z in HBM, atomic window updates,
+    neighbour flags) forced on the same cases reaches the same bar."""
+    X, D, _ = make_problem(w, 35)
+    lam = 0.1 * orc.lambda_max(X, D)
+    tol = 1e-4
+    ref = orc.lgcd(X, D, lam, tol)
+    Xd, Dd = dev(X), dev(D)
+    beta, dtd, _ = pkg.csc_init_beta(Xd, Dd)
+    Z, st = pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, lam, tol, opts=pkg.default_opts(placement=2))
+    assert st["status"] == 0, st
+    assert st["placement"] == 2 and st["workers"] > 1
+    Zh = host(Z)
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    f_gpu = orc.objective(X, D, Zh, lam)
+    assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
+    assert orc.kkt(X, D, Zh, lam) < 1.05 * tol
+    cnt, worst = support_mismatch(Zh, ref["Z"], tol)
+    assert cnt <= max(10, 0.01 * int((ref["Z"] != 0).sum()))
+    assert worst <= 100 * tol

@@ -391,3 +391,24 @@ def test_golden_worked_examples(orc):
         assert out["n_updates"] == c["n_updates"]
         assert abs(orc.objective(X, D, out["Z"], c["lambda"]) - c["objective"]) < 1e-12
         assert abs(orc.lambda_max(X, D) - c["lambda_max"]) < 1e-12
+
+
+@pytest.mark.parametrize("w", [W1D, W2D], ids=["1d", "2d"])
+def test_sampled_routines_match_explicit_model(orc, w):
+    """beta at listed coordinates, beta from Z at listed coordinates and the
+    zero-skipping objective agree with the explicit design matrix."""
+    X, D, Z = _problem(w, 18)
+    Z = Z.astype(np.float64)
+    A = design_matrix(D, w.T)
+    Tz = tuple(t - l + 1 for t, l in zip(w.T, w.L))
+    n = int(np.prod(Tz))
+    rng = np.random.default_rng(4)
+    ks = rng.integers(0, w.K, 40)
+    ss = rng.integers(0, n, 40)
+    cols = ks * n + ss
+    np.testing.assert_allclose(orc.beta_at(X, D, ks, ss), (A.T @ X.ravel())[cols], rtol=0, atol=1e-12)
+    bz = beta_explicit(A, X.ravel(), Z.ravel())
+    np.testing.assert_allclose(orc.beta_from_Z_at(X, D, Z, ks, ss), bz[cols], rtol=0, atol=1e-11)
+    lam = 0.3
+    f = lasso_objective(A, X.ravel(), Z.ravel(), lam)
+    assert abs(orc.objective_sparse(X, D, Z, lam) - f) <= 1e-12 * f
