@@ -157,13 +157,18 @@ __device__ __forceinline__ float sub_prod(float b, float c, float t) { return fm
 
 // Z' = ST(beta, lambda) / ||D_k||^2 (Eq. pb_coord).  FP64 divides (the
 // rounding of the definition); FP32 multiplies by the stored reciprocal.
+// The product is rounded on its own (never contracted into a following
+// subtraction), so |Z' - Z| has the same bits wherever it is evaluated: the
+// owner of a coordinate and a neighbour running the soft-lock test must
+// agree exactly, or a tie between two border candidates is rejected on both
+// sides and neither worker ever updates again.
 __device__ __forceinline__ double coord_update(double beta, double lam, double nrm, double inv) {
     (void)inv;
     return __ddiv_rn(soft_threshold(beta, lam), nrm);
 }
 __device__ __forceinline__ float coord_update(float beta, float lam, float nrm, float inv) {
     (void)nrm;
-    return soft_threshold(beta, lam) * inv;
+    return __fmul_rn(soft_threshold(beta, lam), inv);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
