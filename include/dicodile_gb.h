@@ -182,6 +182,26 @@ CSC_API int cdl_dict_update(const csc_shape *shape, const float *phi, const floa
                     double *objective_out, int *iterations_out, void *workspace,
                     size_t workspace_bytes, csc_stream_t stream);
 
+/* Convolutional dictionary learning, the outer loop of Alg. 2: repeat
+ *   Z <- csc_lgcd_solve(X, D) from Z = 0, lambda = reg * lambda_max(X, D0)
+ *        fixed at the first iteration;
+ *   phi, psi <- cdl_dict_stats(Z, X);
+ *   D <- cdl_dict_update(phi, psi) (pgd_max_iter, pgd_tol)
+ * until the cost 1/2||X - Z*D||^2 + lambda ||Z||_1 after the dictionary step
+ * changes by less than nu (relative) or max_outer iterations are done.
+ *   D: in (D0) / out.  Z, beta, dtd, phi, psi: caller-owned buffers of the
+ *   layouts above (outputs of the last iteration).
+ *   trace: host array of 2 * max_outer doubles (may be NULL): the cost after
+ *   the CSC step and after the dictionary step of every iteration, both from
+ *   the residual with FP64 sums (as csc_objective).
+ *   n_outer: host int (may be NULL): iterations made.
+ * Synchronises `stream` several times per iteration.  Returns
+ * CSC_NOT_CONVERGED if some CSC step did not reach tol. */
+CSC_API int cdl_fit(const csc_shape *shape, const float *X, float *D, float *Z, float *beta, float *dtd,
+                    float *phi, float *psi, double reg, double tol, int max_outer, double nu,
+                    int pgd_max_iter, double pgd_tol, const csc_solve_opts *opts, void *workspace,
+                    size_t workspace_bytes, double *trace, int *n_outer, csc_stream_t stream);
+
 /* FP64 variants of csc_init_beta and csc_lgcd_solve (same layouts, double
  * elements).  They exist to verify the tiled schedule exactly against an FP64
  * reference; they are slow on GB300, whose FP64 rate is low. */

@@ -61,6 +61,7 @@ def _load():
             "orc_beta_at": (None, [i, i, i, i, i, i, p, p, ll, p, p, p]),
             "orc_beta_from_Z_at": (None, [i, i, i, i, i, i, p, p, p, ll, p, p, p]),
             "orc_objective_sparse": (d, [i, i, i, i, i, i, p, p, p, d]),
+            "orc_objective_nz": (d, [i, i, i, i, i, i, p, p, C.c_longlong, p, p, p, p, d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -273,3 +274,35 @@ def beta_from_Z_at(X, D, Z, ks, ss):
 def objective_sparse(X, D, Z, lam: float) -> float:
     X, D, Z = _f64(X), _f64(D), _f64(Z)
     return float(_load().orc_objective_sparse(*_geom(X, D), _ptr(X), _ptr(D), _ptr(Z), float(lam)))
+
+
+def objective_nz(X, D, k, i, j, z, lam: float) -> float:
+    """Eq. csc from the nonzeros of Z given as index arrays (k, i, j) and
+    values z (for 1-D problems i is all zeros and j the position)."""
+    X, D = _f64(X), _f64(D)
+    k, i, j = (np.ascontiguousarray(np.asarray(v), dtype=np.int64) for v in (k, i, j))
+    z = _f64(np.asarray(z))
+    if not (len(k) == len(i) == len(j) == len(z)):
+        raise ValueError("index and value arrays differ in length")
+    return float(_load().orc_objective_nz(*_geom(X, D), _ptr(X), _ptr(D), len(z), _ptr(k), _ptr(i),
+                                          _ptr(j), _ptr(z), float(lam)))
+
+
+def cdl(X, D0, reg: float, tol: float, n_outer: int, pgd_max_iter: int = 50, pgd_tol: float = 1e-8):
+    """The outer loop of Alg. 2 with the routines above: Z by LGCD from zero
+    (lambda = reg * lambda_max(X, D0), fixed), then phi/psi and PGD-Armijo on
+    D.  Returns (D, Z, [(cost after CSC, cost after the dictionary step)])."""
+    X = _f64(X)
+    D = _f64(D0).copy()
+    lam = reg * lambda_max(X, D)
+    L = D.shape[2:]
+    xs = float(np.sum(X ** 2))
+    trace = []
+    Z = None
+    for _ in range(n_outer):
+        Z = lgcd(X, D, lam, tol)["Z"]
+        c1 = objective(X, D, Z, lam)
+        phi, psi = phi_psi(Z, X, L)
+        D, f, _ = pgd_armijo(phi, psi, xs, D, max_iter=pgd_max_iter, tol=pgd_tol)
+        trace.append((c1, f + lam * float(np.abs(Z).sum())))
+    return D, Z, trace

@@ -591,3 +591,30 @@ double orc_objective_sparse(int P, int K, int T0, int T1, int L0, int L1, const 
     free(res);
     return 0.5 * f + lambda * g;
 }
+
+/* The same objective from a list of nonzeros (atom k, row i, column j,
+ * value z) instead of a dense Z, for activation maps too large to hold on
+ * the host in FP64. */
+double orc_objective_nz(int P, int K, int T0, int T1, int L0, int L1, const double *X,
+                        const double *D, long long nnz, const long long *kk, const long long *ii,
+                        const long long *jj, const double *zz, double lambda)
+{
+    size_t nx = (size_t)P * T0 * T1;
+    double *res = malloc(nx * sizeof(double));
+    memcpy(res, X, nx * sizeof(double));
+    double g = 0.0;
+    for (long long n = 0; n < nnz; n++) {
+        int k = (int)kk[n], i = (int)ii[n], j = (int)jj[n];
+        double z = zz[n];
+        if (k < 0 || k >= K) continue;
+        g += fabs(z);
+        for (int p = 0; p < P; p++)
+            for (int a = 0; a < L0; a++)
+                for (int b = 0; b < L1; b++)
+                    res[IDX3(p, i + a, j + b, T0, T1)] -= z * D[IDX4(k, p, a, b, P, L0, L1)];
+    }
+    double f = 0.0;
+    for (size_t q = 0; q < nx; q++) f += res[q] * res[q];
+    free(res);
+    return 0.5 * f + lambda * g;
+}

@@ -58,8 +58,11 @@ class SolveStats(C.Structure):
 
 
 class CscError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    """A failed call; ``stats`` holds the solve statistics when a solve failed."""
+
+    def __init__(self, status: int, where: str, stats: dict | None = None):
         self.status = status
+        self.stats = stats
         msg = status_string(status) if _lib is not None else str(status)
         if status == CSC_ERR_CUDA and _lib is not None:
             msg += f" (cudaError {_lib.csc_last_cuda_error()})"
@@ -93,6 +96,7 @@ def load():
         "csc_objective": (i, [S, p, p, p, d, C.POINTER(d), p, sz, p]),
         "cdl_dict_stats": (i, [S, p, p, p, p, p, sz, p]),
         "cdl_dict_update": (i, [S, p, p, d, p, i, d, C.POINTER(d), C.POINTER(i), p, sz, p]),
+        "cdl_fit": (i, [S, p, p, p, p, p, p, p, d, d, i, d, i, d, O, p, sz, C.POINTER(d), C.POINTER(i), p]),
         "csc_status_string": (C.c_char_p, [i]),
         "csc_last_cuda_error": (i, []),
     }
@@ -108,9 +112,9 @@ def status_string(status: int) -> str:
     return load().csc_status_string(int(status)).decode()
 
 
-def _check(rc: int, where: str, soft=()):
+def _check(rc: int, where: str, soft=(), stats=None):
     if rc != CSC_OK and rc not in soft:
-        raise CscError(rc, where)
+        raise CscError(rc, where, stats)
     return rc
 
 
@@ -236,7 +240,7 @@ def csc_lgcd_solve(X, D, dtd, beta, lam: float, tol: float, Z=None, opts: SolveO
     fn = load().csc_lgcd_solve_f64 if f64 else load().csc_lgcd_solve
     rc = fn(C.byref(s), _ptr(X), _ptr(D), _ptr(dtd), _ptr(beta), _ptr(Z), lam, tol, C.byref(opts),
             _ptr(ws), ws.numel(), C.byref(st), _stream(stream))
-    _check(rc, "csc_lgcd_solve", soft=(CSC_NOT_CONVERGED, CSC_ERR_DIVERGED))
+    _check(rc, "csc_lgcd_solve", soft=(CSC_NOT_CONVERGED, CSC_ERR_DIVERGED), stats=st.as_dict())
     return Z, st.as_dict()
 
 
@@ -285,6 +289,28 @@ def cdl_dict_update(phi, psi, x_sqnorm: float, D, X_shape, max_iter: int = 50, t
                                   int(max_iter), float(tol), C.byref(f), C.byref(it), _ptr(ws),
                                   ws.numel(), _stream(stream)), "cdl_dict_update")
     return f.value, it.value
+
+
+def cdl_fit(X, D, reg: float = 0.1, tol: float = 1e-4, max_outer: int = 10, nu: float = 0.0,
+            pgd_max_iter: int = 50, pgd_tol: float = 1e-8, opts: SolveOpts | None = None, prob=None,
+            stream=None):
+    """Dictionary learning (cdl_fit): D is updated in place.  Returns
+    (Z, trace of (cost after CSC, cost after the dictionary step), status)."""
+    import torch
+    _need(X, torch.float32, "X")
+    _need(D, torch.float32, "D")
+    if prob is None:
+        prob = Problem.create(X, D, opts)
+    s = prob.shape
+    tr = (C.c_double * (2 * max_outer))()
+    n = C.c_int(0)
+    rc = load().cdl_fit(C.byref(s), _ptr(X), _ptr(D), _ptr(prob.Z), _ptr(prob.beta), _ptr(prob.dtd),
+                        _ptr(prob.phi), _ptr(prob.psi), float(reg), float(tol), int(max_outer), float(nu),
+                        int(pgd_max_iter), float(pgd_tol), C.byref(opts) if opts else None,
+                        _ptr(prob.ws), prob.ws.numel(), tr, C.byref(n), _stream(stream))
+    _check(rc, "cdl_fit", soft=(CSC_NOT_CONVERGED,))
+    trace = [(tr[2 * i], tr[2 * i + 1]) for i in range(n.value)]
+    return prob.Z, trace, rc
 
 
 @dataclass

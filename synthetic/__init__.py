@@ -76,20 +76,41 @@ def make_problem(w: Workload, seed: int, D: np.ndarray | None = None):
         D = make_dictionary(rng, w.K, w.P, w.L)
     T = tuple(w.T)
     Tz = tuple(t - l + 1 for t, l in zip(T, w.L))
-    mask = rng.random((w.K,) + Tz) < w.density
-    amp = rng.standard_normal((w.K,) + Tz)
-    if w.nonneg:
-        amp = np.abs(amp)
-    Z = np.where(mask, amp, 0.0)
+    n = int(np.prod(Tz))
+    Z = np.zeros((w.K,) + Tz, dtype=np.float32 if w.density < 0.05 else np.float64)
+    if w.density < 0.05:
+        # i.i.d. Bernoulli(density) per coordinate, drawn as a binomial count
+        # and a uniform subset of positions per atom
+        for k in range(w.K):
+            cnt = int(rng.binomial(n, w.density))
+            pos = rng.choice(n, size=cnt, replace=False)
+            amp = rng.standard_normal(cnt)
+            Z[k].reshape(-1)[pos] = np.abs(amp) if w.nonneg else amp
+    else:
+        mask = rng.random((w.K,) + Tz) < w.density
+        amp = rng.standard_normal((w.K,) + Tz)
+        if w.nonneg:
+            amp = np.abs(amp)
+        Z[...] = np.where(mask, amp, 0.0)
     X = np.zeros((w.P,) + T)
     D64 = D.astype(np.float64)
     for k in range(w.K):
-        if not mask[k].any():
+        idx = np.nonzero(Z[k])
+        nnz = len(idx[0])
+        if nnz == 0:
             continue
-        for p in range(w.P):
-            X[p] += _full_conv(Z[k], D64[k, p])
+        if nnz * int(np.prod(w.L)) < 8 * int(np.prod(Tz)):
+            # sparse map: add each nonzero's shifted atom
+            z = Z[k][idx].astype(np.float64)
+            for off in np.ndindex(*w.L):
+                tgt = tuple(i + o for i, o in zip(idx, off))
+                for p in range(w.P):
+                    np.add.at(X[p], tgt, z * D64[(k, p) + off])
+        else:
+            for p in range(w.P):
+                X[p] += _full_conv(Z[k], D64[k, p])
     X += w.sigma * rng.standard_normal(X.shape)
-    return X.astype(np.float32), D, Z.astype(np.float32)
+    return X.astype(np.float32), D, Z.astype(np.float32, copy=False)
 
 
 def served_sizes(n: int, seed: int, lo: int = 64, hi: int = 2048):

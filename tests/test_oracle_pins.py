@@ -412,3 +412,36 @@ def test_sampled_routines_match_explicit_model(orc, w):
     lam = 0.3
     f = lasso_objective(A, X.ravel(), Z.ravel(), lam)
     assert abs(orc.objective_sparse(X, D, Z, lam) - f) <= 1e-12 * f
+    # the same objective from the list of nonzeros
+    nz = np.nonzero(Z)
+    k, i, j = (nz[0], np.zeros_like(nz[1]), nz[1]) if Z.ndim == 2 else nz
+    assert abs(orc.objective_nz(X, D, k, i, j, Z[nz], lam) - f) <= 1e-12 * f
+
+
+@pytest.mark.parametrize("d0", [0.4, 1.0])
+@pytest.mark.parametrize("dims", [1, 2], ids=["1d", "2d"])
+def test_cdl_loop_one_tap_closed_form(orc, dims, d0):
+    """Alg. 2 with one atom of a single tap (L = 1): the CSC step has the
+    closed form Z = ST(d X, lambda) / d^2 (coordinates decouple) and the
+    dictionary step minimises 1/2 ||X - d Z||^2 over |d| <= 1, so
+    d' = clip(<X, Z> / ||Z||^2, -1, 1).  Two outer iterations; from d = 1 the
+    unconstrained minimiser lies outside the unit ball (projection active)."""
+    rng = np.random.default_rng(21)
+    shape = (1, 300) if dims == 1 else (1, 17, 19)
+    X = rng.standard_normal(shape)
+    D0 = np.full((1, 1) + (1,) * dims, d0)
+    reg = 0.3
+    D, Z, trace = orc.cdl(X, D0, reg, 1e-10, 2, pgd_max_iter=200, pgd_tol=1e-14)
+    x = X.reshape(-1)
+    d = d0
+    lam = reg * abs(d) * np.abs(x).max()
+    costs = []
+    for _ in range(2):
+        z = np.sign(d * x) * np.maximum(np.abs(d * x) - lam, 0.0) / d ** 2
+        c_csc = 0.5 * ((x - d * z) ** 2).sum() + lam * np.abs(z).sum()
+        d = float(np.clip(x @ z / (z @ z), -1.0, 1.0))
+        c_dict = 0.5 * ((x - d * z) ** 2).sum() + lam * np.abs(z).sum()
+        costs.append((c_csc, c_dict))
+    assert abs(float(D.reshape(-1)[0]) - d) <= 1e-9
+    np.testing.assert_allclose(Z.reshape(-1), z, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(np.asarray(trace), np.asarray(costs), rtol=1e-10, atol=0)
