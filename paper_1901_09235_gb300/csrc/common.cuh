@@ -61,6 +61,7 @@ struct alignas(128) WsHeader {
     double pgd_out[12];     // dictionary step: objective, iterations, last step, spare, phase cycles [4..9]
     int scan_total;         // deterministic compaction: total count
     int pad6[15];
+    unsigned long long tphmax[8];      // largest per-worker SM cycles per phase
 };
 
 enum StatIdx { ST_UPDATES = 0, ST_ITERS, ST_REJECTED, ST_SUBTOL, ST_MESSAGES, ST_DEFERRED };
