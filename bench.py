@@ -184,7 +184,8 @@ def lgcd_traffic_per_launch():
     the kernel sources changed since those counters were taken."""
     import hashlib
     prof = os.path.join(ROOT, "profiles", "lgcd_async_kernel_csc1d_T200000_P5_K10_L64.md")
-    src = [os.path.join(ROOT, "paper_1901_09235_gb300", "csrc", f) for f in ("lgcd.cu", "common.cuh")]
+    src = [os.path.join(ROOT, "paper_1901_09235_gb300", "csrc", f)
+           for f in ("lgcd_async.cu", "lgcd_common.cuh", "common.cuh")]
     try:
         text = open(prof).read()
         h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()

@@ -396,10 +396,13 @@ struct Plan {
     size_t smem;
 };
 
-static size_t tile_smem(const Geom &g, int t0, int t1, int rs) {
+// Dynamic shared memory of one tile: beta and Z, the K x K x |window| table
+// and the atom norms, plus a staging buffer for records (PHASED kernel; the
+// asynchronous kernel stages records in its static shared memory).
+static size_t tile_smem(const Geom &g, int t0, int t1, int rs, bool phased) {
     size_t n = (2 * (size_t)g.K * t0 * t1 + (size_t)g.ntab() + 2 * (size_t)g.K) * rs;
     n = (n + 15) & ~(size_t)15;
-    return n + kMsgBatch * sizeof(int4);
+    return phased ? n + kMsgBatch * sizeof(int4) : n;
 }
 
 template <typename real>
@@ -435,7 +438,7 @@ static int smem_per_sm() { return dev_props().smem_sm; }
 // Tile plan.  Full tiles must be at least L_i wide (windows then reach only
 // the adjacent tiles); automatic plans use tiles of at least 2 L_i and the
 // largest number of workers that can all be resident at once.
-static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, size_t static_smem, Plan *pl) {
+static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, size_t static_smem, int max_occ, Plan *pl) {
     const bool d1 = g.d == 1;
     pl->sub0 = d1 ? 1 : (o.sub[0] > 0 ? o.sub[0] : 2 * g.L0);
     pl->sub1 = d1 ? (o.sub[0] > 0 ? o.sub[0] : 2 * g.L1) : (o.sub[1] > 0 ? o.sub[1] : 2 * g.L1);
@@ -453,7 +456,7 @@ static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, size_t stat
         pl->t1 = t1;
         pl->G0 = (int)ceil_div(g.Z0, t0);
         pl->G1 = (int)ceil_div(g.Z1, t1);
-        pl->smem = tile_smem(g, t0, t1, rs);
+        pl->smem = tile_smem(g, t0, t1, rs, o.mode == CSC_MODE_PHASED);
         if (pl->smem + static_smem > (size_t)lim) return CSC_ERR_UNIMPLEMENTED;
         return CSC_OK;
     }
@@ -462,7 +465,7 @@ static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, size_t stat
     bool found = false;
     Plan best{};
     long long best_w = 0;
-    for (int occ = 1; occ <= 8; occ++) {
+    for (int occ = 1; occ <= std::min(8, max_occ); occ++) {
         long long cap_w = (long long)occ * sms;
         if (o.max_workers > 0) cap_w = std::min<long long>(cap_w, o.max_workers);
         size_t budget = std::min<size_t>((size_t)lim - static_smem, (size_t)per_sm / occ - 1024 - static_smem);
@@ -472,7 +475,7 @@ static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, size_t stat
             for (; G1 >= 1; G1--) {
                 int t0 = (int)ceil_div(g.Z0, G0), t1 = (int)ceil_div(g.Z1, G1);
                 int a0 = (int)ceil_div(g.Z0, t0), a1 = (int)ceil_div(g.Z1, t1);
-                if (tile_smem(g, t0, t1, rs) <= budget && nsub(t0, t1) <= max_sub) {
+                if (tile_smem(g, t0, t1, rs, o.mode == CSC_MODE_PHASED) <= budget && nsub(t0, t1) <= max_sub) {
                     long long w = (long long)a0 * a1;
                     // prefer more workers, then squarer tiles
                     bool take = !found || w > best_w ||
@@ -485,7 +488,7 @@ static int make_plan(const Geom &g, const csc_solve_opts &o, int rs, size_t stat
                         best.G1 = a1;
                         best.t0 = t0;
                         best.t1 = t1;
-                        best.smem = tile_smem(g, t0, t1, rs);
+                        best.smem = tile_smem(g, t0, t1, rs, o.mode == CSC_MODE_PHASED);
                     }
                     break;
                 }
@@ -573,8 +576,21 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
             attr_cache.push_back({kern, static_smem});
         }
     }
+    // resident tiles per SM allowed by registers and threads alone
+    int max_occ = 8;
+    if (!global) {
+        static thread_local std::vector<std::pair<const void *, int>> occ_cache;
+        int found_occ = -1;
+        for (auto &c : occ_cache)
+            if (c.first == kern) found_occ = c.second;
+        if (found_occ < 0) {
+            CSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&found_occ, kern, kernel_threads(o.mode, false), 0));
+            occ_cache.push_back({kern, found_occ});
+        }
+        max_occ = std::max(1, found_occ);
+    }
     Plan pl;
-    rc = global ? CSC_ERR_UNIMPLEMENTED : make_plan(g, o, rs, static_smem, &pl);
+    rc = global ? CSC_ERR_UNIMPLEMENTED : make_plan(g, o, rs, static_smem, max_occ, &pl);
     if (rc == CSC_ERR_UNIMPLEMENTED && o.placement == 0 && o.mode != CSC_MODE_PHASED) global = true;
     if (global) {
         kern = kernel_ptr<real>(o.mode, true);

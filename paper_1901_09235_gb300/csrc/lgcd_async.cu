@@ -51,7 +51,6 @@ constexpr int kORing = 64;               // outgoing records
 enum { RESP_WOKEN = 1, RESP_TERMINATE = 2 };
 
 struct AsyncTileState {
-    int dirty[kAsyncMaxSub];          // compute leader only
     int4 in_ring[kInRing];
     int4 out_rec[kORing];
     int out_mask[kORing];
@@ -65,6 +64,7 @@ struct AsyncTileState {
     unsigned p_key[kAW];                       // per-warp argmax key
     unsigned long long p_best[kAW];            // its |dZ| bits
     unsigned long long p_lo[kAW], p_hi[kAW];  // per-warp soft-lock maxima
+    unsigned long long ph[6], t_last, t_pause, tc;  // leader's timeline (SM cycles)
 };
 
 // Order-preserving bits of |dZ| >= 0, plus one (0 stands for "none").
@@ -92,38 +92,74 @@ __device__ __forceinline__ bool near_neighbour(const LgcdArgs<real> &a, const Ti
            (lj < a.L1 - 1 && t.tb > 0) || (lj >= t.wd - (a.L1 - 1) && t.tb < a.G1 - 1);
 }
 
-// Mark the sub-domains that the window of an update at tile-local (li0, lj0)
-// touches inside the tile (compute leader).
+// Exact n / d for 0 <= n < 2^22, d >= 1, from the float reciprocal inv of d
+// (the truncated product is off by at most one either way).
+__device__ __forceinline__ int div_small(int n, int d, float inv) {
+    int q = __float2int_rz(__fmul_rn((float)n, inv));
+    if (q * d > n) q--;
+    else if ((q + 1) * d <= n) q++;
+    return q;
+}
+
+// Warp-wide winner of (largest |dZ|, then smallest key): returns the key
+// (0xffffffff when every lane is empty) and the winner's |dZ| bits + 1.
+__device__ __forceinline__ unsigned warp_argmax(float a, unsigned key, unsigned long long &bits) {
+    const unsigned b = a < 0.f ? 0u : __float_as_uint(a) + 1u;
+    const unsigned m = __reduce_max_sync(0xffffffffu, b);
+    bits = m;
+    if (m == 0u) return 0xffffffffu;
+    return __reduce_min_sync(0xffffffffu, b == m ? key : 0xffffffffu);
+}
+__device__ __forceinline__ unsigned warp_argmax(double a, unsigned key, unsigned long long &bits) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oa = __shfl_xor_sync(0xffffffffu, a, o);
+        const unsigned ok = __shfl_xor_sync(0xffffffffu, key, o);
+        if (oa > a || (oa == a && ok < key)) {
+            a = oa;
+            key = ok;
+        }
+    }
+    bits = a < 0.0 ? 0ull : sl_bits(a);
+    return a < 0.0 ? 0xffffffffu : key;
+}
+
+// Set the bits of the sub-domains that the window of an update at tile-local
+// (li0, lj0) touches inside the tile (compute leader; M <= 64).
 template <typename real, int NT>
-__device__ __forceinline__ void mark_window(const LgcdArgs<real> &a, const Tile<real, NT> &t, AsyncTileState &S,
-                                            int li0, int lj0) {
+__device__ __forceinline__ void mark_window(const LgcdArgs<real> &a, const Tile<real, NT> &t,
+                                            unsigned long long &dmask, int li0, int lj0, float inv0, float inv1) {
     const int ra = max(0, li0 - (a.L0 - 1)), rb = min(t.h - 1, li0 + a.L0 - 1);
     const int ca = max(0, lj0 - (a.L1 - 1)), cb = min(t.wd - 1, lj0 + a.L1 - 1);
     if (ra > rb || ca > cb) return;
-    for (int mr = ra / a.sub0; mr <= rb / a.sub0; mr++)
-        for (int mc = ca / a.sub1; mc <= cb / a.sub1; mc++) S.dirty[mr * t.ns1 + mc] = 1;
+    const int mr1 = div_small(rb, a.sub0, inv0), mc0 = div_small(ca, a.sub1, inv1), mc1 = div_small(cb, a.sub1, inv1);
+    for (int mr = div_small(ra, a.sub0, inv0); mr <= mr1; mr++)
+        for (int mc = mc0; mc <= mc1; mc++) dmask |= 1ull << (mr * t.ns1 + mc);
 }
 
-// Calls fn(k, r, idx, li, lj) for the K x window entries of an update at
-// tile-local (li0, lj0) that lie inside the tile, spread over the compute
-// threads (r = window index, idx = shared-memory index).
+// The K x window entries of an update at tile-local (li0, lj0) that lie
+// inside the tile, spread over the compute threads: fn(k, r, idx, li, lj),
+// r the window index and idx the shared-memory index.  When the window fits
+// the thread count, each thread's window offset is fixed for the whole run.
+struct WinThread {
+    bool fits, on;
+    int r, k0, kstep, di, dj;
+};
 template <typename real, int NT, typename F>
-__device__ __forceinline__ void for_window(const LgcdArgs<real> &a, const Tile<real, NT> &t, int li0, int lj0,
-                                           F fn) {
-    const int tid = threadIdx.x, WW = t.WW;
-    if (WW <= kAsyncCompute) {
-        const int kstep = kAsyncCompute / WW;
-        if (tid >= kstep * WW) return;
-        const int r = tid % WW;
-        const int li = li0 + r / a.W1 - (a.L0 - 1), lj = lj0 + r % a.W1 - (a.L1 - 1);
+__device__ __forceinline__ void for_window(const LgcdArgs<real> &a, const Tile<real, NT> &t, const WinThread &wt,
+                                           int li0, int lj0, float inv_ww, float inv_w1, F fn) {
+    if (wt.fits) {
+        if (!wt.on) return;
+        const int li = li0 + wt.di, lj = lj0 + wt.dj;
         if (li < 0 || li >= t.h || lj < 0 || lj >= t.wd) return;
         const int base = li * a.t1 + lj;
 #pragma unroll 4
-        for (int k = tid / WW; k < t.K; k += kstep) fn(k, r, k * t.TS + base, li, lj);
+        for (int k = wt.k0; k < t.K; k += wt.kstep) fn(k, wt.r, k * t.TS + base, li, lj);
     } else {
-        for (int q = tid; q < t.K * WW; q += kAsyncCompute) {
-            const int k = q / WW, r = q % WW;
-            const int li = li0 + r / a.W1 - (a.L0 - 1), lj = lj0 + r % a.W1 - (a.L1 - 1);
+        for (int q = threadIdx.x; q < t.K * t.WW; q += kAsyncCompute) {
+            const int k = div_small(q, t.WW, inv_ww), r = q - k * t.WW;
+            const int di = div_small(r, a.W1, inv_w1);
+            const int li = li0 + di - (a.L0 - 1), lj = lj0 + (r - di * a.W1) - (a.L1 - 1);
             if (li < 0 || li >= t.h || lj < 0 || lj >= t.wd) continue;
             fn(k, r, k * t.TS + li * a.t1 + lj, li, lj);
         }
@@ -140,7 +176,6 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
     const int ns0 = (t.h + a.sub0 - 1) / a.sub0, M = ns0 * t.ns1;
     const unsigned long long t_start = globaltimer_ns(), c_start = clock64();
     const unsigned long long deadline = t_start + a.timeout_ns;
-    if (threadIdx.x < kAsyncMaxSub) S.dirty[threadIdx.x] = threadIdx.x < M ? 1 : 0;
     if (threadIdx.x == 0) {
         S.in_head = S.in_tail = S.out_head = S.out_tail = 0;
         S.idle_seq = S.resp_seq = S.resp_kind = 0;
@@ -283,25 +318,54 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
         for (int k = 0; k < a.K; k++) g = fmin(g, 50.0 / a.dmax[k]);
         guard = real(g);
     }
-    long long n_upd = 0, n_it = 0, n_rej = 0, n_sub = 0, n_def = 0, n_step = 0;
-    unsigned long long ph[6] = {0, 0, 0, 0, 0, 0}, t_last = 0, t_pause = 0;
-    unsigned long long tc = clock64(), tn;
-    int cursor = 0, par = 0;
-    for (;; par ^= 1) {
-        // ---- top: the leader picks the next piece of work
+    const float inv_sub0 = 1.f / a.sub0, inv_sub1 = 1.f / a.sub1, inv_K = 1.f / t.K;
+    const float inv_t0 = 1.f / a.t0, inv_t1 = 1.f / a.t1, inv_W1 = 1.f / a.W1, inv_WW = 1.f / t.WW;
+    // fixed per-thread offsets: window entry (r, first atom) and position in a
+    // full sub-domain (dr, dc, first atom)
+    WinThread wt;
+    wt.fits = t.WW <= kAsyncCompute;
+    wt.kstep = wt.fits ? kAsyncCompute / t.WW : 1;
+    wt.on = wt.fits && tid < wt.kstep * t.WW;
+    wt.r = wt.fits ? tid % t.WW : 0;
+    wt.k0 = wt.fits ? tid / t.WW : 0;
+    wt.di = wt.r / a.W1 - (a.L0 - 1);
+    wt.dj = wt.r % a.W1 - (a.L1 - 1);
+    const int nbf = a.sub0 * a.sub1;
+    const bool s_fits = nbf <= kAsyncCompute;
+    const int s_kstep = s_fits ? kAsyncCompute / nbf : 1;
+    const bool s_on = s_fits && tid < s_kstep * nbf;
+    const int s_r = s_fits ? tid % nbf : 0, s_k0 = s_fits ? tid / nbf : 0;
+    const int s_dr = s_r / a.sub1, s_dc = s_r % a.sub1;
+    // counters and the timeline are the leader's (thread 0)
+    int n_upd = 0, n_it = 0, n_rej = 0, n_sub = 0, n_def = 0, n_step = 0;
+    if (tid == 0) {
+        for (int i = 0; i < 6; i++) S.ph[i] = 0;
+        S.t_last = S.t_pause = 0;
+        S.tc = clock64();
+    }
+    auto lap = [&](int i) {
         if (tid == 0) {
-            int nm = S.in_head - S.in_tail, m = -1, bstop = S.stop;
+            const unsigned long long c = clock64();
+            S.ph[i] += c - S.tc;
+            S.tc = c;
+        }
+    };
+    // leader state: dirty sub-domains as a bit mask, cyclic cursor, inbox tail
+    unsigned long long dmask = M >= 64 ? ~0ull : ((1ull << M) - 1ull);
+    int cursor = 0, in_tail = 0, par = 0;
+    for (;; par ^= 1) {
+        // ---- top: the leader picks the next piece of work; this barrier
+        // also closes the previous step's window update
+        if (tid == 0) {
+            int nm = S.in_head - in_tail, m = -1, bstop = S.stop;
             while (!bstop && nm == 0) {
-                for (int i = 0; i < M; i++) {
-                    const int j = cursor + i < M ? cursor + i : cursor + i - M;
-                    if (S.dirty[j]) {
-                        m = j;
-                        break;
-                    }
+                if (dmask) {
+                    const unsigned long long x = dmask >> cursor;
+                    m = x ? cursor + __ffsll((long long)x) - 1 : __ffsll((long long)dmask) - 1;
+                    break;
                 }
-                if (m >= 0) break;
                 // nothing to do: pause until a record arrives or every tile is done
-                if (!t_pause) t_pause = globaltimer_ns();
+                if (!S.t_pause) S.t_pause = globaltimer_ns();
                 const unsigned long long tp = clock64();
                 const int seq = S.idle_seq + 1;
                 __threadfence_block();
@@ -315,12 +379,12 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
                     }
                     __nanosleep(64);
                 }
-                ph[5] += clock64() - tp;
+                S.ph[5] += clock64() - tp;
                 bstop = S.stop || S.resp_kind == RESP_TERMINATE;
-                nm = S.in_head - S.in_tail;
+                nm = S.in_head - in_tail;
             }
             if (m >= 0 && nm == 0) {
-                S.dirty[m] = 0;
+                dmask &= ~(1ull << m);
                 cursor = m + 1 < M ? m + 1 : 0;
             }
             S.b_m[par] = nm == 0 ? m : -1;
@@ -328,118 +392,115 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
             S.b_stop[par] = bstop;
         }
         cbar();
-        tn = clock64();
-        ph[0] += tn - tc;
-        tc = tn;
+        lap(0);
         const int bstop = S.b_stop[par], nmsg = S.b_nmsg[par], m = S.b_m[par];
         if (bstop) break;
         n_step++;
         if (nmsg > 0) {
             // ---- neighbour updates (Alg. 3 "receive messages and update beta")
-            const int base = S.in_tail;
+            const int base = in_tail;  // equal in every thread: the leader's copy
             for (int i = 0; i < nmsg; i++) {
                 const int4 msg = S.in_ring[(base + i) & (kInRing - 1)];
                 real dz;
                 unpack_msg(msg, dz);
-                const int li0 = msg.y / a.Z1 - t.or0, lj0 = msg.y % a.Z1 - t.oc0;
-                const real *row = t.sdtd + (size_t)msg.x * t.K * t.WW;
-                for_window<real, NT>(a, t, li0, lj0, [&](int k, int r, int idx, int, int) {
-                    atomicAdd(&t.sbeta[idx], -(row[k * t.WW + r] * dz));
+                const int gi = div_small(msg.y, a.Z1, 1.f / a.Z1);
+                const int li0 = gi - t.or0, lj0 = msg.y - gi * a.Z1 - t.oc0;
+                const int kmsg = msg.x;
+                for_window<real, NT>(a, t, wt, li0, lj0, inv_WW, inv_W1, [&](int k, int r, int idx, int, int) {
+                    const real c = t.sdtd[((size_t)kmsg * t.K + k) * t.WW + r];
+                    atomicAdd(&t.sbeta[idx], -(c * dz));
                 });
             }
             cbar();
             for (int i = 0; i < nmsg; i++) {
                 const int4 msg = S.in_ring[(base + i) & (kInRing - 1)];
-                const int li0 = msg.y / a.Z1 - t.or0, lj0 = msg.y % a.Z1 - t.oc0;
-                for_window<real, NT>(a, t, li0, lj0, [&](int k, int, int idx, int li, int lj) {
+                const int gi = div_small(msg.y, a.Z1, 1.f / a.Z1);
+                const int li0 = gi - t.or0, lj0 = msg.y - gi * a.Z1 - t.oc0;
+                for_window<real, NT>(a, t, wt, li0, lj0, inv_WW, inv_W1, [&](int k, int, int idx, int li, int lj) {
                     if (near_neighbour<real, NT>(a, t, li, lj))
                         st_relaxed(a.beta + k * plane + (size_t)(t.or0 + li) * a.Z1 + t.oc0 + lj, t.sbeta[idx]);
                 });
-                if (tid == 0) mark_window<real, NT>(a, t, S, li0, lj0);
+                if (tid == 0) mark_window<real, NT>(a, t, dmask, li0, lj0, inv_sub0, inv_sub1);
             }
             cbar();
+            in_tail = base + nmsg;
             if (tid == 0) {
                 __threadfence_block();
-                S.in_tail = base + nmsg;
+                S.in_tail = in_tail;
             }
-            tn = clock64();
-            ph[1] += tn - tc;
-            tc = tn;
+            lap(1);
             continue;
         }
         if (m < 0) continue;
         // ---- candidate scan of C_m (Eq. pb_coord) with the oracle's tie-break
-        const int mr = m / t.ns1, mc = m % t.ns1;
+        const int mr = div_small(m, t.ns1, 1.f / t.ns1), mc = m - mr * t.ns1;
         const int r0 = mr * a.sub0, c0 = mc * a.sub1;
         const int bh = min(a.sub0, t.h - r0), bw = min(a.sub1, t.wd - c0), nb = bh * bw;
         real ba = real(-1);
         unsigned bkey = 0xffffffffu;
-        if (nb <= kAsyncCompute) {
-            const int kstep = kAsyncCompute / nb;
-            if (tid < kstep * nb) {
-                const int r = tid % nb;
-                const int li = r0 + r / bw, lj = c0 + r % bw;
-                const int base = li * a.t1 + lj;
-                const unsigned pos = (unsigned)base * (unsigned)t.K;
+        auto consider = [&](int base, int k) {
+            const int idx = base + k * t.TS;
+            const real d = abs_real(coord_update(t.sbeta[idx], a.lambda, t.snrm[k], t.sinv[k]) - t.sz[idx]);
+            const unsigned key = (unsigned)base * (unsigned)t.K + (unsigned)k;
+            if (d > ba || (d == ba && key < bkey)) {
+                ba = d;
+                bkey = key;
+            }
+        };
+        if (s_fits && bh == a.sub0 && bw == a.sub1) {
+            if (s_on) {
+                const int base = (r0 + s_dr) * a.t1 + c0 + s_dc;
 #pragma unroll 4
-                for (int k = tid / nb; k < t.K; k += kstep) {
-                    const int idx = base + k * t.TS;
-                    const real d =
-                        abs_real(coord_update(t.sbeta[idx], a.lambda, t.snrm[k], t.sinv[k]) - t.sz[idx]);
-                    const unsigned key = pos + (unsigned)k;
-                    if (d > ba || (d == ba && key < bkey)) {
-                        ba = d;
-                        bkey = key;
+                for (int k = s_k0; k < t.K; k += s_kstep) consider(base, k);
+            }
+        } else {
+            const float inv_nb = 1.f / nb, inv_bw = 1.f / bw;
+            for (int q = tid; q < t.K * nb; q += kAsyncCompute) {
+                const int k = div_small(q, nb, inv_nb), r = q - k * nb;
+                const int dr = div_small(r, bw, inv_bw);
+                consider((r0 + dr) * a.t1 + c0 + (r - dr * bw), k);
+            }
+        }
+        unsigned long long best_bits = 0;
+        unsigned best_key = 0xffffffffu;
+        {
+            unsigned long long wb;
+            const unsigned wkey = warp_argmax(ba, bkey, wb);
+            if constexpr (sizeof(real) == 4) {
+                // (bits, ~key) packed: the largest packed value is the winner
+                if (lane == 0) S.p_best[warp] = wkey == 0xffffffffu ? 0ull : (wb << 32) | (0xffffffffu - wkey);
+                cbar();
+                unsigned long long pk = 0;
+#pragma unroll
+                for (int w = 0; w < kAW; w++) pk = S.p_best[w] > pk ? S.p_best[w] : pk;
+                best_bits = pk >> 32;
+                best_key = 0xffffffffu - (unsigned)(pk & 0xffffffffull);
+            } else {
+                if (lane == 0) {
+                    S.p_key[warp] = wkey;
+                    S.p_best[warp] = wkey == 0xffffffffu ? 0ull : wb;
+                }
+                cbar();
+#pragma unroll
+                for (int w = 0; w < kAW; w++) {
+                    const unsigned long long bb = S.p_best[w];
+                    const unsigned kk = S.p_key[w];
+                    if (bb > best_bits || (bb == best_bits && bb != 0 && kk < best_key)) {
+                        best_bits = bb;
+                        best_key = kk;
                     }
                 }
             }
-        } else {
-            for (int q = tid; q < t.K * nb; q += kAsyncCompute) {
-                const int k = q / nb, r = q % nb;
-                const int li = r0 + r / bw, lj = c0 + r % bw;
-                const int base = li * a.t1 + lj;
-                const int idx = base + k * t.TS;
-                const real d = abs_real(coord_update(t.sbeta[idx], a.lambda, t.snrm[k], t.sinv[k]) - t.sz[idx]);
-                const unsigned key = (unsigned)base * (unsigned)t.K + (unsigned)k;
-                if (d > ba || (d == ba && key < bkey)) {
-                    ba = d;
-                    bkey = key;
-                }
-            }
-        }
-        {
-            const unsigned wkey = warp_argmax_key(ba, bkey);
-            // the winning lane's |dZ| bits travel with the key
-            const unsigned long long mine_bits = (bkey == wkey && wkey != 0xffffffffu) ? sl_bits(ba) : 0ull;
-            const unsigned long long wb = warp_max_u64(mine_bits, 0);
-            if (lane == 0) {
-                S.p_key[warp] = wkey;
-                S.p_best[warp] = wb;
-            }
-        }
-        cbar();
-        unsigned long long best_bits = 0;
-        unsigned best_key = 0xffffffffu;
-#pragma unroll
-        for (int w = 0; w < kAW; w++) {
-            const unsigned long long b = S.p_best[w];
-            const unsigned k = S.p_key[w];
-            if (b > best_bits || (b == best_bits && b != 0 && k < best_key)) {
-                best_bits = b;
-                best_key = k;
-            }
         }
         n_it++;
-        tn = clock64();
-        ph[2] += tn - tc;
-        tc = tn;
+        lap(2);
         if (best_bits == 0) {
             n_sub++;
             continue;
         }
-        const unsigned pos = best_key / (unsigned)t.K;
-        const int k0 = (int)(best_key % (unsigned)t.K);
-        const int li0 = (int)(pos / (unsigned)a.t1), lj0 = (int)(pos % (unsigned)a.t1);
+        const int pos = div_small((int)best_key, t.K, inv_K);
+        const int k0 = (int)best_key - pos * t.K;
+        const int li0 = div_small(pos, a.t1, inv_t1), lj0 = pos - li0 * a.t1;
         const int idx0 = k0 * t.TS + li0 * a.t1 + lj0;
         const real znew = coord_update(t.sbeta[idx0], a.lambda, t.snrm[k0], t.sinv[k0]);
         const real dz = znew - t.sz[idx0];
@@ -459,7 +520,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
                 const int gi0 = t.or0 + li0 - (a.L0 - 1), gj0 = t.oc0 + lj0 - (a.L1 - 1);
                 const int WW = t.WW, KW = t.K * WW;
                 const int kinc = kAsyncCompute / WW, rinc = kAsyncCompute - kinc * WW;
-                int k = tid / WW, r = tid - k * WW;
+                int k = wt.fits ? wt.k0 : tid / WW, r = wt.fits ? wt.r : tid % WW;
                 for (int base = tid; base < KW; base += B * kAsyncCompute) {
                     real vb[B], vz[B];
                     int kk[B], side[B];
@@ -469,15 +530,17 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
                         kk[u] = k;
                         vb[u] = vz[u] = real(0);
                         if (base + u * kAsyncCompute < KW) {
-                            const int di = r / a.W1;
+                            const int di = div_small(r, a.W1, inv_W1);
                             const int gi = gi0 + di, gj = gj0 + (r - di * a.W1);
                             const bool in_dom = gi >= 0 && gi < a.Z0 && gj >= 0 && gj < a.Z1;
-                            const bool in_tile = gi >= t.or0 && gi < t.or0 + t.h && gj >= t.oc0 && gj < t.oc0 + t.wd;
+                            const bool in_tile =
+                                gi >= t.or0 && gi < t.or0 + t.h && gj >= t.oc0 && gj < t.oc0 + t.wd;
                             if (in_dom && !in_tile) {
                                 const size_t g = k * plane + (size_t)gi * a.Z1 + gj;
                                 vb[u] = __ldcg(a.beta + g);
                                 vz[u] = __ldcg(a.Z + g);
-                                side[u] = (gi / a.t0) * a.G1 + gj / a.t1 < t.w ? 1 : 2;
+                                const int owner = div_small(gi, a.t0, inv_t0) * a.G1 + div_small(gj, a.t1, inv_t1);
+                                side[u] = owner < t.w ? 1 : 2;
                             }
                         }
                         k += kinc;
@@ -490,14 +553,20 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
 #pragma unroll
                     for (int u = 0; u < B; u++) {
                         if (!side[u]) continue;
-                        const unsigned long long b = sl_bits(
+                        const unsigned long long bb = sl_bits(
                             abs_real(coord_update(vb[u], a.lambda, t.snrm[kk[u]], t.sinv[kk[u]]) - vz[u]));
-                        if (side[u] == 1) lo = b > lo ? b : lo;
-                        else hi = b > hi ? b : hi;
+                        if (side[u] == 1) lo = bb > lo ? bb : lo;
+                        else hi = bb > hi ? bb : hi;
                     }
                 }
-                lo = warp_max_u64(lo, 0);
-                hi = warp_max_u64(hi, 0);
+                if constexpr (sizeof(real) == 4) {
+                    // |dZ| bits + 1 fit 32 bits in FP32
+                    lo = __reduce_max_sync(0xffffffffu, (unsigned)lo);
+                    hi = __reduce_max_sync(0xffffffffu, (unsigned)hi);
+                } else {
+                    lo = warp_max_u64(lo, 0);
+                    hi = warp_max_u64(hi, 0);
+                }
             }
             if (lane == 0) {
                 S.p_lo[warp] = lo;
@@ -517,24 +586,23 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
             }
             const unsigned long long mine = sl_bits(adz);
             const bool accept = mine > mlo && mine >= mhi;
-            tn = clock64();
-            ph[3] += tn - tc;
-            tc = tn;
+            lap(3);
             if (!accept || !S.b_ok) {
                 if (tid == 0) {
-                    S.dirty[m] = 1;  // try again later
+                    dmask |= 1ull << m;  // try again later
                     if (!accept) n_rej++;
                     else n_def++;
                 }
                 continue;
             }
         }
-        // ---- beta window update (Eq. beta_update), border entries published
+        // ---- beta window update (Eq. beta_update), border entries published;
+        // the next step's top barrier closes it
         {
-            const real *row = t.sdtd + (size_t)k0 * t.K * t.WW;
-            for_window<real, NT>(a, t, li0, lj0, [&](int k, int r, int idx, int li, int lj) {
+            for_window<real, NT>(a, t, wt, li0, lj0, inv_WW, inv_W1, [&](int k, int r, int idx, int li, int lj) {
                 if (k == k0 && li == li0 && lj == lj0) return;
-                const real v = sub_prod(t.sbeta[idx], row[k * t.WW + r], dz);
+                const real c = t.sdtd[((size_t)k0 * t.K + k) * t.WW + r];
+                const real v = sub_prod(t.sbeta[idx], c, dz);
                 t.sbeta[idx] = v;
                 if (near_neighbour<real, NT>(a, t, li, lj))
                     st_relaxed(a.beta + k * plane + (size_t)(t.or0 + li) * a.Z1 + t.oc0 + lj, v);
@@ -544,7 +612,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
             t.sz[idx0] = znew;
             const int gpos = (t.or0 + li0) * a.Z1 + t.oc0 + lj0;
             if (border) st_relaxed(a.Z + k0 * plane + gpos, znew);
-            mark_window<real, NT>(a, t, S, li0, lj0);
+            mark_window<real, NT>(a, t, dmask, li0, lj0, inv_sub0, inv_sub1);
             if (nd > 0) {
                 int mask = 0;
                 for (int i = 0; i < nd; i++) mask |= 1 << dl[i];
@@ -555,17 +623,14 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
                 S.out_head = oh + 1;
             }
             n_upd++;
-            t_last = clock64();
+            S.t_last = clock64();
             if (a.max_updates > 0) {
                 const unsigned long long prev = atomicAdd(&a.hdr->updates_total, 1ull);
                 if ((long long)prev + 1 >= a.max_updates) set_stop(a.hdr, CSC_NOT_CONVERGED);
             }
             if (a.guard_on && abs_real(znew) > guard) set_stop(a.hdr, CSC_ERR_DIVERGED);
         }
-        cbar();
-        tn = clock64();
-        ph[4] += tn - tc;
-        tc = tn;
+        lap(4);
     }
     // wait (bounded) for the communication warp before the tile is written back
     if (tid == 0) {
@@ -588,17 +653,17 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_DEFERRED], (unsigned long long)n_def);
         atomicMax(&a.hdr->wmax[0], (unsigned long long)n_step);
         atomicMax(&a.hdr->wmax[1], (unsigned long long)n_upd);
-        if (t_last) {
+        if (S.t_last) {
             // SM cycles of the last update converted with this tile's own clock rate
             const unsigned long long c_end = clock64(), g_end = globaltimer_ns();
             const double ns_per_cycle = c_end > c_start ? (double)(g_end - t_start) / (double)(c_end - c_start) : 0.0;
-            atomicMax(&a.hdr->tmax[0], (unsigned long long)((double)(t_last - c_start) * ns_per_cycle));
+            atomicMax(&a.hdr->tmax[0], (unsigned long long)((double)(S.t_last - c_start) * ns_per_cycle));
         }
         atomicMax(&a.hdr->tmax[1], globaltimer_ns() - t_start);
-        if (t_pause) atomicMax(&a.hdr->tmax[2], t_pause - t_start);
+        if (S.t_pause) atomicMax(&a.hdr->tmax[2], S.t_pause - t_start);
         for (int i = 0; i < 6; i++) {
-            atomicAdd(&a.hdr->tph[i], ph[i]);
-            atomicMax(&a.hdr->tphmax[i], ph[i]);
+            atomicAdd(&a.hdr->tph[i], S.ph[i]);
+            atomicMax(&a.hdr->tphmax[i], S.ph[i]);
         }
     }
 }
