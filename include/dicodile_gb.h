@@ -172,7 +172,9 @@ CSC_API int cdl_dict_stats(const csc_shape *shape, const float *Z, const float *
  * backtracking, gradient phi * D - psi, projection D_k /= max(1, ||D_k||_2).
  * The first step is 1 / max_k sum_k2 sum_delta |phi_{k,k2}[delta]|, each later
  * iteration starts from twice the last accepted step; at most max_iter
- * iterations, stop when ||D+ - D|| < tol ||D||.
+ * iterations, stop when ||D+ - D|| < tol ||D||.  D is held in FP32, so a
+ * relative change below 4 x 2^-24 cannot be resolved: a smaller tol acts as
+ * 4 x 2^-24.
  *   D: in/out.  x_sqnorm: ||X||_2^2.  objective_out: host pointer (may be
  *   NULL) receiving F(D) = 1/2||X - Z*D||^2 at the end (FP64);
  *   iterations_out: host pointer (may be NULL).

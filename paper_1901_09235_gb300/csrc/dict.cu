@@ -246,9 +246,11 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
 //
 // Layout: one thread-block cluster, CTA r owns atoms [r ka, (r+1) ka).  Its
 // D and G slices live in shared memory, its per-source convolutions QD/QG in
-// global scratch; the new G and the per-atom scalars / Gram rows are
-// exchanged through distributed shared memory (two cluster barriers per
-// iteration).
+// shared memory when they fit (else global scratch).  Every CTA also holds
+// the full G and every atom's scalars / Gram rows: their owners write them
+// into each CTA's shared memory (distributed shared memory stores) before a
+// cluster barrier, so after the barrier they are read locally (two cluster
+// barriers per iteration).
 struct PgdArgs {
     const float *phi, *psi;
     float *D;      // in/out
@@ -258,9 +260,10 @@ struct PgdArgs {
     int K, P, L0, L1, max_iter, ka, stage_phi, q_in_smem;
 };
 
-constexpr int kPgdThreads = 1024;
+constexpr int kPgdThreads = 512;
 constexpr int kPgdWarps = kPgdThreads / 32;
 constexpr int kPgdMaxK = 32;
+constexpr float kPgdMinTol = 4.0f / 16777216.0f;  // 4 x 2^-24
 
 // Block-wide sum returned to every thread (warp 0 combines the warp sums).
 __device__ __forceinline__ double block_reduce_sum(double v, double *scratch) {
@@ -269,98 +272,94 @@ __device__ __forceinline__ double block_reduce_sum(double v, double *scratch) {
     if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double s = warp_sum(scratch[threadIdx.x]);
+        double s = warp_sum(threadIdx.x < kPgdWarps ? scratch[threadIdx.x] : 0.0);
         if (threadIdx.x == 0) scratch[kPgdWarps] = s;
     }
     __syncthreads();
     return scratch[kPgdWarps];
 }
 
-// Three block-wide sums at once, returned to every thread.
-__device__ __forceinline__ void block_reduce3(double &x, double &y, double &z, double (*scr)[kPgdWarps + 1]) {
-    x = warp_sum(x);
-    y = warp_sum(y);
-    z = warp_sum(z);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-        scr[0][threadIdx.x >> 5] = x;
-        scr[1][threadIdx.x >> 5] = y;
-        scr[2][threadIdx.x >> 5] = z;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const double a0 = warp_sum(scr[0][threadIdx.x]), a1 = warp_sum(scr[1][threadIdx.x]),
-                     a2 = warp_sum(scr[2][threadIdx.x]);
-        if (threadIdx.x == 0) {
-            scr[0][kPgdWarps] = a0;
-            scr[1][kPgdWarps] = a1;
-            scr[2][kPgdWarps] = a2;
-        }
-    }
-    __syncthreads();
-    x = scr[0][kPgdWarps];
-    y = scr[1][kPgdWarps];
-    z = scr[2][kPgdWarps];
-}
-
 // out[k2][e] = sum_tau2 phi_{k,k2}[tau - tau2] src[k2][p][tau2] for the own
-// output entries e = (k, p, tau) and every source atom k2.  Consecutive
-// threads take consecutive tau, so the phi row is read without conflicts and
-// the source value is a broadcast.
-__device__ __forceinline__ void conv_per_source(const PgdArgs &a, const float *sphi, int k_lo, int nown,
-                                                const float *src, float *out) {
-    // work item = (source k2, own row (kl, p, ta), chunk of 32 consecutive tb):
-    // one warp per item, lane = tb; the phi row is read without bank
-    // conflicts and the source value is a broadcast
+// output entries e = (kl, p, tau) of this CTA and every source atom k2
+// (per-source stride own_cap).  One warp per (k2, kl, chunk of 64 positions
+// of the L0 x L1 plane); each lane keeps two positions (o, o + 32) for up to
+// eight channels, so one phi value serves every channel and one source value
+// (a broadcast) serves two positions.
+__device__ __forceinline__ void conv_per_source(const PgdArgs &a, const float *sphi, int k_lo, int nk,
+                                                const float *src, float *out, int own_cap) {
     const int LL = a.L0 * a.L1, per = a.P * LL;
     const int W1 = 2 * a.L1 - 1, WW = (2 * a.L0 - 1) * W1;
-    const int rows = nown / a.L1, chunks = (a.L1 + 31) / 32;
-    const int items = a.K * rows * chunks;
+    const int chunks = (LL + 63) / 64;
+    const int items = a.K * nk * chunks;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int it = warp; it < items; it += kPgdWarps) {
-        const int k2 = it / (rows * chunks), rem = it % (rows * chunks);
-        const int row = rem / chunks, tb = (rem % chunks) * 32 + lane;
-        const int kl = row / (a.P * a.L0), pr = row % (a.P * a.L0), p = pr / a.L0, ta = pr % a.L0;
+        const int k2 = it / (nk * chunks), rem = it - k2 * (nk * chunks);
+        const int kl = rem / chunks, ch = rem - kl * chunks;
         const float *__restrict__ ph =
             (a.stage_phi ? sphi + (size_t)kl * a.K * WW : a.phi + (size_t)(k_lo + kl) * a.K * WW) + (size_t)k2 * WW;
-        const float *__restrict__ sv = src + (size_t)k2 * per + p * LL;
-        float acc0 = 0.f, acc1 = 0.f;
-        if (tb < a.L1) {
+        const float *__restrict__ sv = src + (size_t)k2 * per;
+        const int o0 = ch * 64 + lane, o1 = o0 + 32;
+        const bool v0 = o0 < LL, v1 = o1 < LL;
+        // phi index of position (ta, tb) and tap (a2, b2): base(ta, tb) - (a2 W1 + b2)
+        const int base0 = v0 ? (o0 / a.L1 + a.L0 - 1) * W1 + o0 % a.L1 + a.L1 - 1 : 0;
+        const int base1 = v1 ? (o1 / a.L1 + a.L0 - 1) * W1 + o1 % a.L1 + a.L1 - 1 : 0;
+        float *__restrict__ dst = out + (size_t)k2 * own_cap + (size_t)kl * per;
+        for (int pc = 0; pc < a.P; pc += 8) {
+            const int np = min(8, a.P - pc);
+            float acc0[8], acc1[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) acc0[j] = acc1[j] = 0.f;
             for (int a2 = 0; a2 < a.L0; a2++) {
-                const float *__restrict__ prow = ph + (ta - a2 + a.L0 - 1) * W1 + tb + a.L1 - 1;
-                const float *__restrict__ srow = sv + a2 * a.L1;
+                const float *__restrict__ srow = sv + (size_t)pc * LL + a2 * a.L1;
+                const int off = a2 * W1;
                 int b2 = 0;
-                for (; b2 + 1 < a.L1; b2 += 2) {
-                    acc0 = fmaf(prow[-b2], srow[b2], acc0);
-                    acc1 = fmaf(prow[-b2 - 1], srow[b2 + 1], acc1);
+                if ((LL & 3) == 0 && (a.L1 & 3) == 0) {
+                    // four taps at a time: the source values of every channel as one
+                    // 16-byte load each, the eight phi values, then the products
+                    for (; b2 < a.L1; b2 += 4) {
+                        float f0[4], f1[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            f0[u] = v0 ? ph[base0 - off - b2 - u] : 0.f;
+                            f1[u] = v1 ? ph[base1 - off - b2 - u] : 0.f;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            if (j < np) {
+                                const float4 g = *reinterpret_cast<const float4 *>(srow + (size_t)j * LL + b2);
+                                acc0[j] = fmaf(f0[0], g.x, acc0[j]);
+                                acc1[j] = fmaf(f1[0], g.x, acc1[j]);
+                                acc0[j] = fmaf(f0[1], g.y, acc0[j]);
+                                acc1[j] = fmaf(f1[1], g.y, acc1[j]);
+                                acc0[j] = fmaf(f0[2], g.z, acc0[j]);
+                                acc1[j] = fmaf(f1[2], g.z, acc1[j]);
+                                acc0[j] = fmaf(f0[3], g.w, acc0[j]);
+                                acc1[j] = fmaf(f1[3], g.w, acc1[j]);
+                            }
+                        }
+                    }
                 }
-                if (b2 < a.L1) acc0 = fmaf(prow[-b2], srow[b2], acc0);
-            }
-            out[(size_t)k2 * nown + (size_t)row * a.L1 + tb] = acc0 + acc1;
-        }
-    }
-}
-
-// gall[e] = (rank owning entry e).pub[e - its first entry], for all n
-// entries: every remote load of a thread is issued before any store.
-__device__ __forceinline__ void gather_full(cg::cluster_group &cl, const float *pub, float *gall, int n, int per,
-                                            int ka) {
-    constexpr int U = 8;
-    for (int base = threadIdx.x; base < n; base += U * kPgdThreads) {
-        float v[U];
+#pragma unroll 4
+                for (; b2 < a.L1; b2++) {
+                    const float f0 = v0 ? ph[base0 - off - b2] : 0.f;
+                    const float f1 = v1 ? ph[base1 - off - b2] : 0.f;
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int e = base + u * kPgdThreads;
-            v[u] = 0.f;
-            if (e < n) {
-                const int r = (e / per) / ka;
-                v[u] = cl.map_shared_rank(pub, (unsigned)r)[e - r * ka * per];
+                    for (int j = 0; j < 8; j++) {
+                        if (j < np) {
+                            const float g = srow[(size_t)j * LL + b2];
+                            acc0[j] = fmaf(f0, g, acc0[j]);
+                            acc1[j] = fmaf(f1, g, acc1[j]);
+                        }
+                    }
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int e = base + u * kPgdThreads;
-            if (e < n) gall[e] = v[u];
+            for (int j = 0; j < 8; j++) {
+                if (j < np) {
+                    if (v0) dst[(size_t)(pc + j) * LL + o0] = acc0[j];
+                    if (v1) dst[(size_t)(pc + j) * LL + o1] = acc1[j];
+                }
+            }
         }
     }
 }
@@ -374,25 +373,28 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     const int k_lo = min(K, rank * a.ka), k_hi = min(K, k_lo + a.ka);
     const int nk = k_hi - k_lo, nown = nk * per, e0 = k_lo * per;
     const int own_cap = a.ka * per;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // dynamic shared memory
+    // dynamic shared memory; every CTA holds the full G and every atom's
+    // scalars / Gram rows, written by their owners before a cluster barrier
     double *sa = reinterpret_cast<double *>(smem_raw), *sb = sa + K, *sc = sb + K;
-    double *pubsc = sc + K;                       // [2][ka][3 + 3K] own scalars and Gram rows
     const int rowlen = 3 + 3 * K;
-    float *gall = reinterpret_cast<float *>(pubsc + 2 * (size_t)a.ka * rowlen);
+    double *allsc = sc + K;                       // [K][rowlen]
+    // the float section starts on a 16-byte boundary (vector loads of G)
+    const size_t dbytes = ((3 * (size_t)K + (size_t)K * rowlen) * sizeof(double) + 15) & ~(size_t)15;
+    float *gall = reinterpret_cast<float *>(smem_raw + dbytes);
     float *sD = gall + n, *sG = sD + own_cap;
-    float *pubG = sG + own_cap;                   // [2][own_cap]
-    float *sphi = pubG + 2 * (size_t)own_cap;
+    float *sphi = sG + own_cap;
     float *qsm = sphi + (a.stage_phi ? (size_t)a.ka * K * WW : 0);
     float *qd = a.q_in_smem ? qsm : a.qd + (size_t)rank * K * own_cap;
     float *qg = a.q_in_smem ? qsm + (size_t)K * own_cap : a.qg + (size_t)rank * K * own_cap;
 
     __shared__ double scratch[kPgdWarps + 1];
-    __shared__ double scr3[3][kPgdWarps + 1];
     __shared__ float s_alpha[kPgdMaxK], s_beta[kPgdMaxK], s_scale[kPgdMaxK];
+    __shared__ float fsa[kPgdMaxK], fsa1[kPgdMaxK], fsb[kPgdMaxK], fsc[kPgdMaxK];
     __shared__ float fMDD[kPgdMaxK * kPgdMaxK], fMDG[kPgdMaxK * kPgdMaxK], fMGG[kPgdMaxK * kPgdMaxK];
     __shared__ double s_ctl[4];  // eta, dsq, dnorm, stop
-    int par = 0;
+    __shared__ double s_lip;
 
     // stage own slices and phi rows; the full D is the first convolution input
     for (int e = threadIdx.x; e < nown; e += kPgdThreads) sD[e] = a.D[e0 + e];
@@ -409,55 +411,53 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
             t += fabs((double)a.phi[(size_t)(k_lo + kl) * K * WW + q]);
         lip_loc = fmax(lip_loc, block_reduce_sum(t, scratch));
     }
-    // QD = phi * D per source; G = sum_k2 QD_k2 - psi
-    conv_per_source(a, sphi, k_lo, nown, gall, qd);
+    if (threadIdx.x == 0) s_lip = lip_loc;
+    // QD = phi * D per source; G = sum_k2 QD_k2 - psi, written to every CTA's full G
+    conv_per_source(a, sphi, k_lo, nk, gall, qd, own_cap);
     __syncthreads();
+    cl.sync();  // every CTA has finished reading D from its full copy
     for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
         float g = -a.psi[e0 + e];
         for (int k2 = 0; k2 < K; k2++) g += qd[(size_t)k2 * own_cap + e];
         sG[e] = g;
-        pubG[e] = g;
+        for (int r = 0; r < ncl; r++) cl.map_shared_rank(gall, (unsigned)r)[e0 + e] = g;
     }
-    // publish lip for the cluster max (slot 0 of the scalar rows)
-    if (threadIdx.x == 0) pubsc[0] = lip_loc;
     cl.sync();
     double lip = 0.0;
-    for (int r = 0; r < ncl; r++) lip = fmax(lip, cl.map_shared_rank(pubsc, r)[0]);
-    // full G for the first QG convolution
-    gather_full(cl, pubG, gall, n, per, a.ka);
-    __syncthreads();
+    for (int r = 0; r < ncl; r++) lip = fmax(lip, *cl.map_shared_rank(&s_lip, (unsigned)r));
 
-    // (re)compute QG from gall, then own scalars and Gram rows, then share them
+    // QG = phi * G per source, then the own atoms' scalars and Gram rows,
+    // written to every CTA; after the barrier they are read locally
     unsigned long long ph[6] = {0, 0, 0, 0, 0, 0}, tc = clock64(), tn;
 #define PGD_TICK(i)      \
     tn = clock64();      \
     ph[i] += tn - tc;    \
     tc = tn;
     auto refresh_stats = [&]() {
-        conv_per_source(a, sphi, k_lo, nown, gall, qg);
+        conv_per_source(a, sphi, k_lo, nk, gall, qg, own_cap);
         __syncthreads();
         PGD_TICK(4)
-        double *mine = pubsc + (size_t)par * a.ka * rowlen;
-        for (int kl = 0; kl < nk; kl++) {
-            const float *d = sD + kl * per, *g = sG + kl * per;
-            float v[3] = {0.f, 0.f, 0.f};
-            for (int e = threadIdx.x; e < per; e += kPgdThreads) {
-                v[0] = fmaf(d[e], d[e], v[0]);
-                v[1] = fmaf(d[e], g[e], v[1]);
-                v[2] = fmaf(g[e], g[e], v[2]);
-            }
-            double r0 = v[0], r1 = v[1], r2 = v[2];
-            block_reduce3(r0, r1, r2, scr3);
-            if (threadIdx.x == 0) {
-                mine[kl * rowlen + 0] = r0;
-                mine[kl * rowlen + 1] = r1;
-                mine[kl * rowlen + 2] = r2;
-            }
-            // Gram rows: warp w takes sources k2 = w, w + 32, ...
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            for (int k2 = warp; k2 < K; k2 += kPgdWarps) {
-                const float *qdr = qd + (size_t)k2 * own_cap + kl * per;
-                const float *qgr = qg + (size_t)k2 * own_cap + kl * per;
+        // rows: warp w handles (own atom kl, item i) pairs; item 0 = the three
+        // FP64 scalars, items 1..K = the Gram entries of source k2 = i - 1
+        for (int q = warp; q < nk * (K + 1); q += kPgdWarps) {
+            const int kl = q / (K + 1), i = q - kl * (K + 1);
+            const float *d = sD + (size_t)kl * per, *g = sG + (size_t)kl * per;
+            double v0, v1, v2;
+            if (i == 0) {
+                double x0 = 0.0, x1 = 0.0, x2 = 0.0;
+                for (int e = lane; e < per; e += 32) {
+                    const double dv = d[e], gv = g[e];
+                    x0 = fma(dv, dv, x0);
+                    x1 = fma(dv, gv, x1);
+                    x2 = fma(gv, gv, x2);
+                }
+                v0 = warp_sum(x0);
+                v1 = warp_sum(x1);
+                v2 = warp_sum(x2);
+            } else {
+                const int k2 = i - 1;
+                const float *qdr = qd + (size_t)k2 * own_cap + (size_t)kl * per;
+                const float *qgr = qg + (size_t)k2 * own_cap + (size_t)kl * per;
                 float dd = 0.f, dg = 0.f, gg = 0.f;
                 for (int e = lane; e < per; e += 32) {
                     dd = fmaf(d[e], qdr[e], dd);
@@ -469,26 +469,44 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
                     dg += __shfl_xor_sync(0xffffffffu, dg, o);
                     gg += __shfl_xor_sync(0xffffffffu, gg, o);
                 }
-                if (lane == 0) {
-                    mine[kl * rowlen + 3 + k2] = dd;
-                    mine[kl * rowlen + 3 + K + k2] = dg;
-                    mine[kl * rowlen + 3 + 2 * K + k2] = gg;
+                v0 = dd;
+                v1 = dg;
+                v2 = gg;
+            }
+            // lanes 0 .. ncl-1 write the three values to one CTA each
+            const int k = k_lo + kl;
+            for (int r = lane; r < ncl; r += 32) {
+                double *dst = cl.map_shared_rank(allsc, (unsigned)r) + (size_t)k * rowlen;
+                if (i == 0) {
+                    dst[0] = v0;
+                    dst[1] = v1;
+                    dst[2] = v2;
+                } else {
+                    dst[3 + (i - 1)] = v0;
+                    dst[3 + K + (i - 1)] = v1;
+                    dst[3 + 2 * K + (i - 1)] = v2;
                 }
             }
         }
         cl.sync();
         for (int q = threadIdx.x; q < K * rowlen; q += kPgdThreads) {
-            const int k = q / rowlen, i = q % rowlen;
-            const int r = k / a.ka, kl = k % a.ka;
-            const double v = cl.map_shared_rank(pubsc + (size_t)par * a.ka * rowlen, r)[kl * rowlen + i];
-            if (i == 0) sa[k] = v;
-            else if (i == 1) sb[k] = v;
-            else if (i == 2) sc[k] = v;
+            const int k = q / rowlen, i = q - k * rowlen;
+            const double v = allsc[q];
+            if (i == 0) {
+                sa[k] = v;
+                fsa[k] = (float)v;
+                fsa1[k] = (float)(v - 1.0);  // ||D_k||^2 - 1 before rounding
+            } else if (i == 1) {
+                sb[k] = v;
+                fsb[k] = (float)v;
+            } else if (i == 2) {
+                sc[k] = v;
+                fsc[k] = (float)v;
+            }
             else if (i < 3 + K) fMDD[k * K + (i - 3)] = (float)v;
             else if (i < 3 + 2 * K) fMDG[k * K + (i - 3 - K)] = (float)v;
             else fMGG[k * K + (i - 3 - 2 * K)] = (float)v;
         }
-        par ^= 1;
         __syncthreads();
     };
     refresh_stats();
@@ -497,33 +515,35 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     int it = 0;
     if (lip > 0.0) {
         for (it = 0; it < a.max_iter; it++) {
-            // Armijo backtracking by warp 0 on the scalars (FP32 terms, FP64 sums)
+            // Armijo backtracking by warp 0 on the per-atom scalars, in FP32:
+            // with delta_k = ||D_k - eta G_k||^2 - 1 = (||D_k||^2 - 1)
+            // - 2 eta <D_k, G_k> + eta^2 ||G_k||^2 (the first term taken from the
+            // FP64 sum) and s_k = 1 / sqrt(1 + delta_k), the scale deviation
+            // s_k - 1 = -delta_k s_k^2 / (1 + s_k) has no cancellation
             if (threadIdx.x < 32) {
-                const int lane = threadIdx.x;
-                double e_try = it > 0 ? 2.0 * eta : eta, dsq = 0.0, dnorm = 0.0;
+                float e_try = it > 0 ? 2.0f * (float)eta : (float)eta, dsq = 0.f, dnorm = 0.f;
                 {
-                    double dn = 0.0;
-                    for (int k = lane; k < K; k += 32) dn += sa[k];
-                    dnorm = warp_sum(dn);
+                    float dn = 0.f;
+                    for (int k = lane; k < K; k += 32) dn += fsa[k];
+                    for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+                    dnorm = dn;
                 }
                 for (int bt = 0; bt < 60; bt++) {
-                    double ds = 0.0;
+                    float ds = 0.f;
                     for (int k = lane; k < K; k += 32) {
-                        // scale 1 / max(1, ||D_k - eta G_k||): FP32 rsqrt refined by
-                        // two Newton steps in FP64 (multiplies only)
-                        const double nn = sa[k] - 2.0 * e_try * sb[k] + e_try * e_try * sc[k];
-                        double sk = 1.0;
-                        if (nn > 1.0) {
-                            double r = (double)rsqrtf((float)nn);
-                            r = r * (1.5 - 0.5 * nn * r * r);
-                            r = r * (1.5 - 0.5 * nn * r * r);
+                        const float delta = fsa1[k] + e_try * (e_try * fsc[k] - 2.0f * fsb[k]);
+                        float sk = 1.f, al = 0.f;
+                        if (delta > 0.f) {
+                            float r = rsqrtf(1.f + delta);
+                            r = r * (1.5f - 0.5f * (1.f + delta) * r * r);  // one Newton step
                             sk = r;
+                            al = -delta * r * r / (1.f + r);
                         }
-                        const double al = sk - 1.0, be = -sk * e_try;
-                        ds += al * al * sa[k] + 2.0 * al * be * sb[k] + be * be * sc[k];
-                        s_scale[k] = (float)sk;
-                        s_alpha[k] = (float)al;
-                        s_beta[k] = (float)be;
+                        const float be = -sk * e_try;
+                        ds += al * (al * fsa[k] + 2.f * be * fsb[k]) + be * be * fsc[k];
+                        s_scale[k] = sk;
+                        s_alpha[k] = al;
+                        s_beta[k] = be;
                     }
                     __syncwarp();
                     float qf = 0.f;
@@ -532,25 +552,31 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
                         const float al = s_alpha[k], be = s_beta[k], al2 = s_alpha[k2], be2 = s_beta[k2];
                         qf += al * (al2 * fMDD[q] + be2 * fMDG[q]) + be * (al2 * fMDG[k2 * K + k] + be2 * fMGG[q]);
                     }
-                    for (int o = 16; o > 0; o >>= 1) qf += __shfl_xor_sync(0xffffffffu, qf, o);
-                    dsq = warp_sum(ds);
-                    if ((double)qf * e_try <= dsq || bt == 59) break;
-                    e_try *= 0.5;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        qf += __shfl_xor_sync(0xffffffffu, qf, o);
+                        ds += __shfl_xor_sync(0xffffffffu, ds, o);
+                    }
+                    dsq = ds;
+                    if (qf * e_try <= dsq || bt == 59) break;
+                    e_try *= 0.5f;
                     __syncwarp();
                 }
                 if (lane == 0) {
                     s_ctl[0] = e_try;
                     s_ctl[1] = dsq;
                     s_ctl[2] = dnorm;
-                    s_ctl[3] = sqrt(dsq) < a.tol * sqrt(dnorm) ? 1.0 : 0.0;
+                    // a relative change below the FP32 resolution of D is noise
+                    const float tol = fmaxf((float)a.tol, kPgdMinTol);
+                    s_ctl[3] = sqrtf(dsq) < tol * sqrtf(dnorm) ? 1.0 : 0.0;
                 }
             }
             __syncthreads();
             PGD_TICK(0)
             eta = s_ctl[0];
             const float feta = (float)eta;
-            // accept: D+ = D + alpha D + beta G; G+ = G + sum_k2 (alpha QD + beta QG); QD+ linear
-            float *pg = pubG + (size_t)par * own_cap;
+            const bool stop = s_ctl[3] != 0.0;
+            // accept: D+ = D + alpha D + beta G; G+ = G + sum_k2 (alpha QD + beta QG),
+            // written to every CTA's full G; QD+ linear
             for (int e = threadIdx.x; e < nown; e += kPgdThreads) {
                 const int k = k_lo + e / per;
                 const float d = sD[e], g = sG[e];
@@ -563,19 +589,16 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
                     qd[o] = s_scale[k2] * fmaf(-feta, qgv, qdv);
                 }
                 sG[e] = gn;
-                pg[e] = gn;
+                if (!stop)
+                    for (int r = 0; r < ncl; r++) cl.map_shared_rank(gall, (unsigned)r)[e0 + e] = gn;
             }
-            const bool stop = s_ctl[3] != 0.0;
             PGD_TICK(1)
             if (stop) {
                 it++;
                 break;
             }
-            cl.sync();  // every rank's new G is published
+            cl.sync();  // every CTA's full G is complete
             PGD_TICK(2)
-            gather_full(cl, pubG + (size_t)par * own_cap, gall, n, per, a.ka);
-            __syncthreads();
-            PGD_TICK(3)
             refresh_stats();
             PGD_TICK(5)
         }
@@ -599,8 +622,8 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     if (rank == 0 && threadIdx.x == 0) {
         double tp = 0.0, tg = 0.0;
         for (int r = 0; r < ncl; r++) {
-            tp += cl.map_shared_rank(fin, r)[0];
-            tg += cl.map_shared_rank(fin, r)[1];
+            tp += cl.map_shared_rank(fin, (unsigned)r)[0];
+            tg += cl.map_shared_rank(fin, (unsigned)r)[1];
         }
         a.out[0] = 0.5 * a.x_sqnorm - 0.5 * tp + 0.5 * tg;
         a.out[1] = (double)it;
@@ -609,12 +632,13 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     }
     cl.sync();  // keep every rank's shared memory alive until all reads are done
 }
+#undef PGD_TICK
 
 static size_t pgd_smem(const Geom &g, int ka, bool stage, bool qsm) {
     const long long per = (long long)g.P * g.L0 * g.L1, n = g.nd();
     const int K = g.K, rowlen = 3 + 3 * K;
-    size_t d = (3 * (size_t)K + 2 * (size_t)ka * rowlen) * sizeof(double);
-    size_t f = ((size_t)n + 4 * (size_t)ka * per + (stage ? (size_t)ka * K * g.nw() : 0) +
+    size_t d = ((3 * (size_t)K + (size_t)K * rowlen) * sizeof(double) + 15) & ~(size_t)15;
+    size_t f = ((size_t)n + 2 * (size_t)ka * per + (stage ? (size_t)ka * K * g.nw() : 0) +
                 (qsm ? 2 * (size_t)K * ka * per : 0)) *
                sizeof(float);
     return d + f;
