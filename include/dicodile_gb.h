@@ -85,6 +85,9 @@ typedef struct {
     int warm_start;       /* 1 = Z and beta on entry are a consistent starting point        */
     int placement;        /* 0 = automatic, 1 = tiles in shared memory, 2 = tiles in global
                              memory (used when a tile's beta, Z and table do not fit)      */
+    int beta_init;        /* cdl_fit: 0 = beta-init in FP32 (csc_init_beta), 1 = on the
+                             tensor cores in split bf16 (csc_init_beta_bf16x3) after the
+                             first iteration, whose exact beta also fixes lambda          */
 } csc_solve_opts;
 
 typedef struct {
@@ -203,6 +206,21 @@ CSC_API int cdl_fit(const csc_shape *shape, const float *X, float *D, float *Z, 
                     float *phi, float *psi, double reg, double tol, int max_outer, double nu,
                     int pgd_max_iter, double pgd_tol, const csc_solve_opts *opts, void *workspace,
                     size_t workspace_bytes, double *trace, int *n_outer, csc_stream_t stream);
+
+/* csc_init_beta with the correlation on the tensor cores (tcgen05) in
+ * split-bf16 precision: each X and D value is split into bf16 hi + lo parts
+ * and beta accumulates hi*hi + hi*lo + lo*hi in FP32 (the mixed-precision
+ * beta-init of Alg. 1's initialisation).  Elementwise
+ *   |beta - beta_exact| <= (2^-16 + 2 gamma_n) sum_p sum_tau |D_kp[tau]| |X_p[s+tau]|,
+ * n = P L0 roundup(L1, 16).  dtd is computed in FP32 as in csc_init_beta.
+ * lambda_max_out (may be NULL) receives max |beta| of this beta (same error
+ * bound); the call then synchronises `stream`.  Returns CSC_ERR_UNIMPLEMENTED
+ * when the split dictionary (4 x roundup(K, 16) x P L0 roundup(L1, 16) bytes)
+ * and two operand chunks do not fit in one CTA's shared memory or K > 256,
+ * CSC_ERR_TIMEOUT when a device wait gave up. */
+CSC_API int csc_init_beta_bf16x3(const csc_shape *shape, const float *X, const float *D, float *beta,
+                                 float *dtd, double *lambda_max_out, void *workspace,
+                                 size_t workspace_bytes, csc_stream_t stream);
 
 /* FP64 variants of csc_init_beta and csc_lgcd_solve (same layouts, double
  * elements).  They exist to verify the tiled schedule exactly against an FP64

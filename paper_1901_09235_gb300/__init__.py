@@ -33,7 +33,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("tile", C.c_int * 2), ("sub", C.c_int * 2), ("mode", C.c_int),
                 ("max_workers", C.c_int), ("max_updates", C.c_longlong),
                 ("timeout_s", C.c_double), ("beta_refresh", C.c_int),
-                ("divergence_guard", C.c_int), ("warm_start", C.c_int), ("placement", C.c_int)]
+                ("divergence_guard", C.c_int), ("warm_start", C.c_int), ("placement", C.c_int),
+                ("beta_init", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -91,6 +92,7 @@ def load():
         "csc_workspace_size": (i, [S, O, C.POINTER(sz)]),
         "csc_init_beta": (i, [S, p, p, p, p, C.POINTER(d), p, sz, p]),
         "csc_init_beta_f64": (i, [S, p, p, p, p, C.POINTER(d), p, sz, p]),
+        "csc_init_beta_bf16x3": (i, [S, p, p, p, p, C.POINTER(d), p, sz, p]),
         "csc_lgcd_solve": (i, [S, p, p, p, p, p, C.c_float, C.c_float, O, p, sz, ST, p]),
         "csc_lgcd_solve_f64": (i, [S, p, p, p, p, p, d, d, O, p, sz, ST, p]),
         "csc_objective": (i, [S, p, p, p, d, C.POINTER(d), p, sz, p]),
@@ -217,6 +219,26 @@ def csc_init_beta(X, D, beta=None, dtd=None, ws=None, stream=None, want_lambda_m
            "csc_init_beta")
     return beta, dtd, (lm.value if want_lambda_max else None)
 
+
+
+def csc_init_beta_bf16x3(X, D, beta=None, dtd=None, ws=None, stream=None, want_lambda_max=True):
+    """csc_init_beta with the correlation on the tensor cores in split-bf16
+    precision (csc_init_beta_bf16x3); float32 tensors only."""
+    import torch
+    _need(X, torch.float32, "X")
+    _need(D, torch.float32, "D")
+    s = make_shape(tuple(X.shape), tuple(D.shape))
+    if beta is None:
+        beta = torch.empty(z_shape(s), dtype=torch.float32, device=X.device)
+    if dtd is None:
+        dtd = torch.empty(tab_shape(s), dtype=torch.float32, device=X.device)
+    if ws is None:
+        ws = workspace(s, device=X.device)
+    lm = C.c_double(0.0)
+    _check(load().csc_init_beta_bf16x3(C.byref(s), _ptr(X), _ptr(D), _ptr(beta), _ptr(dtd),
+                                       C.byref(lm) if want_lambda_max else None, _ptr(ws), ws.numel(),
+                                       _stream(stream)), "csc_init_beta_bf16x3")
+    return beta, dtd, (lm.value if want_lambda_max else None)
 
 def csc_lgcd_solve(X, D, dtd, beta, lam: float, tol: float, Z=None, opts: SolveOpts | None = None,
                    ws=None, stream=None):

@@ -52,12 +52,17 @@ extern "C" int cdl_fit(const csc_shape *shape, const float *X, float *D, float *
     csc_solve_opts o;
     csc_default_opts(&o);
     if (opts) o = *opts;
+    if (o.beta_init < 0 || o.beta_init > 1) return CSC_ERR_INVALID;
     o.warm_start = 0;  // Z = 0 at every CSC step (Alg. 1 / Alg. 3 initialisation)
     double lambda = 0.0, prev = 0.0;
     int q = 0, status = CSC_OK;
     for (q = 0; q < max_outer; q++) {
         double lmax = 0.0;
-        rc = csc_init_beta(shape, X, D, beta, dtd, q == 0 ? &lmax : nullptr, ws, ws_bytes, stream);
+        // the first beta is exact (it fixes lambda); later ones may run on the tensor cores
+        if (q > 0 && o.beta_init == 1)
+            rc = csc_init_beta_bf16x3(shape, X, D, beta, dtd, nullptr, ws, ws_bytes, stream);
+        else
+            rc = csc_init_beta(shape, X, D, beta, dtd, q == 0 ? &lmax : nullptr, ws, ws_bytes, stream);
         if (rc) return rc;
         if (q == 0) lambda = (double)(float)(reg * lmax);  // fixed from D0, as the solver receives it
         csc_solve_stats S;

@@ -51,6 +51,25 @@ def test_cdl_small_matches_oracle(pkg, orc):
     _monotone(tr)
 
 
+def test_cdl_small_mixed_precision_matches_oracle(pkg, orc):
+    """The same loop with the beta-init of every iteration after the first on
+    the tensor cores (split bf16): each solve still ends on a beta recomputed
+    in FP32, so the costs match the oracle's loop as closely as in FP32."""
+    w = Workload("cdl96", P=1, K=4, T=(96, 96), L=(8, 8), density=5e-3, sigma=0.05, nonneg=True)
+    X, D0, _ = make_problem(w, 41)
+    rng = np.random.default_rng(5)
+    D0 = D0 + 0.3 * rng.standard_normal(D0.shape).astype(np.float32)
+    D0 /= np.sqrt((D0.reshape(w.K, -1) ** 2).sum(1)).reshape(-1, 1, 1, 1)
+    _, _, tr_ref = orc.cdl(X, D0, 0.1, 1e-4, 3, pgd_max_iter=20)
+    opts = pkg.default_opts(beta_init=1)
+    Z, tr, rc = pkg.cdl_fit(dev(X), dev(D0), reg=0.1, tol=1e-4, max_outer=3, pgd_max_iter=20, opts=opts)
+    assert rc == 0 and len(tr) == 3
+    for (a, b), (ra, rb) in zip(tr, tr_ref):
+        assert abs(a - ra) <= 1e-4 * abs(ra)
+        assert abs(b - rb) <= 1e-4 * abs(rb)
+    _monotone(tr)
+
+
 def test_cdl_small_repeated_solves_terminate(pkg):
     """Exact ties between border candidates of neighbouring tiles are common
     late in a solve on this problem (|dZ| values near tol are coarsely
