@@ -222,6 +222,73 @@ CSC_API int csc_init_beta_bf16x3(const csc_shape *shape, const float *X, const f
                                  float *dtd, double *lambda_max_out, void *workspace,
                                  size_t workspace_bytes, csc_stream_t stream);
 
+/* beta recomputed from scratch for a given Z (Eq. beta_update's invariant:
+ * beta_k = D~_k * (X - Z*D) + ||D_k||^2 Z_k), with max |dZ| over every
+ * coordinate (the KKT test of Alg. 1's stop) and the objective of Eq. csc,
+ * both accumulated from FP64 sums.  beta: out.  max_dz_out, objective_out:
+ * host pointers (may be NULL); the call synchronises `stream`. */
+CSC_API int csc_refresh_beta(const csc_shape *shape, const float *X, const float *D, const float *Z,
+                             float lambda, float *beta, double *max_dz_out, double *objective_out,
+                             void *workspace, size_t workspace_bytes, csc_stream_t stream);
+
+/* Batched solves: many images of uneven size in one persistent launch.
+ * A persistent grid (two CTAs of 256 threads per SM) takes the tiles of queued
+ * images (jobs) in order and runs the global-memory LGCD worker (Alg. 3) on
+ * each; an image starts when all of its tiles are held.  Images share the atom
+ * shape, the resident dictionary D and its D^T D table.  Jobs are appended
+ * while the kernel runs; completion is reported through pinned host memory.
+ * Every device wait is bounded by run_seconds. */
+typedef struct csc_queue csc_queue;
+
+/* Device and pinned-host workspace for a queue (atoms: d = 2, P, K, L; T is
+ * ignored) holding up to max_jobs jobs in total, ctl_slots of them at once. */
+CSC_API int csc_queue_workspace_size(const csc_shape *atoms, int max_jobs, int ctl_slots,
+                                     size_t *device_bytes, size_t *host_bytes);
+
+/* Start the persistent kernel on kernel_stream.  D [K][P][L0][L1] and dtd
+ * (from csc_init_beta) stay resident and must outlive the queue.
+ * device_workspace: caller-owned device memory; host_workspace: caller-owned
+ * pinned host memory the device can write (cudaHostAlloc / pinned tensors).
+ * side_stream carries the control copies.  Both streams must be distinct and
+ * created with cudaStreamNonBlocking (CSC_ERR_INVALID otherwise): the kernel
+ * runs until csc_queue_close, and the legacy default stream waits for every
+ * blocking stream.  The kernel takes the largest shared-memory carveout, and
+ * the library's beta-init, refresh and objective kernels are loaded before it
+ * starts, so that they run beside it on every SM.  Other kernels that first
+ * load while the queue runs may wait for it to end (lazy module loading). 
+ * opts: tile / sub-domain sizes, mode, timeout of each solve (may be NULL).
+ * The library allocates only the host-side handle. */
+CSC_API int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd,
+                             const csc_solve_opts *opts, int max_jobs, int ctl_slots,
+                             void *device_workspace, size_t device_bytes, void *host_workspace,
+                             size_t host_bytes, double run_seconds, csc_stream_t kernel_stream,
+                             csc_stream_t side_stream, csc_queue **queue_out);
+
+/* Queue one image of T0 x T1 samples: beta [K][Z0][Z1] must hold D~ * X (from
+ * csc_init_beta, or a consistent warm state with warm_start = 1, in which
+ * case Z is kept; otherwise Z is zeroed).  beta and Z belong to the caller and
+ * are updated in place until the job completes.  job_out: index for
+ * csc_queue_poll.  The image is cut into at most opts.max_workers tiles
+ * (default: 7/8 of the grid, so that small jobs start beside a large one).
+ * CSC_ERR_WORKSPACE when max_jobs or ctl_slots is used up (poll finished
+ * jobs to free control slots). */
+CSC_API int csc_queue_submit(csc_queue *queue, int T0, int T1, float *beta, float *Z, float lambda,
+                             float tol, int warm_start, int *job_out);
+
+/* 1 when the job has completed (stats filled: status, updates, iterations,
+ * rejected, messages, device time in kernel_ms), 0 while it runs, negative
+ * status on a bad argument.  Host-only, no CUDA call. */
+CSC_API int csc_queue_poll(csc_queue *queue, int job, csc_solve_stats *stats);
+
+/* The device-side state of a job, for diagnosing a stalled queue: out[8] =
+ * {first slot, tiles W, tiles taken, tiles finished, jobs published, next
+ * slot, grid size, completion word}.  Synchronises the side stream. */
+CSC_API int csc_queue_inspect(csc_queue *queue, int job, long long *out);
+
+/* No more jobs: wait until the queue drains, stop the kernel, release the
+ * handle. */
+CSC_API int csc_queue_close(csc_queue *queue);
+
 /* FP64 variants of csc_init_beta and csc_lgcd_solve (same layouts, double
  * elements).  They exist to verify the tiled schedule exactly against an FP64
  * reference; they are slow on GB300, whose FP64 rate is low. */

@@ -99,6 +99,13 @@ def load():
         "cdl_dict_stats": (i, [S, p, p, p, p, p, sz, p]),
         "cdl_dict_update": (i, [S, p, p, d, p, i, d, C.POINTER(d), C.POINTER(i), p, sz, p]),
         "cdl_fit": (i, [S, p, p, p, p, p, p, p, d, d, i, d, i, d, O, p, sz, C.POINTER(d), C.POINTER(i), p]),
+        "csc_refresh_beta": (i, [S, p, p, p, C.c_float, p, C.POINTER(d), C.POINTER(d), p, sz, p]),
+        "csc_queue_workspace_size": (i, [S, i, i, C.POINTER(sz), C.POINTER(sz)]),
+        "csc_queue_create": (i, [S, p, p, O, i, i, p, sz, p, sz, d, p, p, C.POINTER(p)]),
+        "csc_queue_submit": (i, [p, i, i, p, p, C.c_float, C.c_float, i, C.POINTER(i)]),
+        "csc_queue_poll": (i, [p, i, ST]),
+        "csc_queue_close": (i, [p]),
+        "csc_queue_inspect": (i, [p, i, C.POINTER(C.c_longlong)]),
         "csc_status_string": (C.c_char_p, [i]),
         "csc_last_cuda_error": (i, []),
     }
@@ -277,6 +284,130 @@ def csc_objective(X, D, Z, lam: float, ws=None, stream=None) -> float:
     _check(load().csc_objective(C.byref(s), _ptr(X), _ptr(D), _ptr(Z), float(lam), C.byref(out),
                                 _ptr(ws), ws.numel(), _stream(stream)), "csc_objective")
     return out.value
+
+
+def csc_refresh_beta(X, D, Z, lam: float, beta=None, ws=None, stream=None):
+    """beta recomputed from scratch for Z, with max |dZ| (the KKT test) and
+    the objective (csc_refresh_beta).  Returns (beta, max_dz, objective)."""
+    import torch
+    for t, n in ((X, "X"), (D, "D"), (Z, "Z")):
+        _need(t, torch.float32, n)
+    s = make_shape(tuple(X.shape), tuple(D.shape))
+    if beta is None:
+        beta = torch.empty(z_shape(s), dtype=torch.float32, device=X.device)
+    _need(beta, torch.float32, "beta")
+    if ws is None:
+        ws = workspace(s, device=X.device)
+    mdz, obj = C.c_double(0.0), C.c_double(0.0)
+    _check(load().csc_refresh_beta(C.byref(s), _ptr(X), _ptr(D), _ptr(Z), float(lam), _ptr(beta),
+                                   C.byref(mdz), C.byref(obj), _ptr(ws), ws.numel(), _stream(stream)),
+           "csc_refresh_beta")
+    return beta, mdz.value, obj.value
+
+
+class Queue:
+    """Many 2-D solves of uneven size in one persistent launch (csc_queue_*).
+
+    D (K, P, L0, L1) and its D^T D table stay resident.  Each job brings its
+    own beta (from csc_init_beta*, ready on the submitting stream) and Z, which
+    the kernel updates in place.  The kernel runs on its own stream and the
+    control copies on a second one; both are non-blocking streams.  While the
+    queue is open nothing may wait for the whole device (torch.cuda.synchronize,
+    the legacy default stream of a blocking stream): the kernel ends only on
+    close() or after run_seconds."""
+
+    def __init__(self, D, dtd, max_jobs: int = 1024, ctl_slots: int = 256, run_seconds: float = 120.0,
+                 opts: SolveOpts | None = None):
+        import torch
+        _need(D, torch.float32, "D")
+        _need(dtd, torch.float32, "dtd")
+        if D.dim() != 4:
+            raise ValueError("D must be (K, P, L0, L1)")
+        K, P, L0, L1 = D.shape
+        s = Shape()
+        s.d, s.P, s.K = 2, P, K
+        s.T[0], s.T[1], s.L[0], s.L[1] = L0, L1, L0, L1
+        self.atoms, self.D, self.dtd = s, D, dtd
+        lib = load()
+        db, hb = C.c_size_t(0), C.c_size_t(0)
+        _check(lib.csc_queue_workspace_size(C.byref(s), int(max_jobs), int(ctl_slots), C.byref(db),
+                                            C.byref(hb)), "csc_queue_workspace_size")
+        self.ws = torch.empty(db.value, dtype=torch.uint8, device=D.device)
+        self.host = torch.zeros(hb.value, dtype=torch.uint8, pin_memory=True)
+        self.kernel_stream = torch.cuda.Stream(device=D.device)
+        self.side_stream = torch.cuda.Stream(device=D.device)
+        self.side_stream.wait_stream(torch.cuda.current_stream(D.device))
+        self.kernel_stream.wait_stream(torch.cuda.current_stream(D.device))
+        self._opts = opts
+        self._jobs = {}
+        h = C.c_void_p(0)
+        _check(lib.csc_queue_create(C.byref(s), _ptr(D), _ptr(dtd), C.byref(opts) if opts else None,
+                                    int(max_jobs), int(ctl_slots), _ptr(self.ws), self.ws.numel(),
+                                    C.c_void_p(self.host.data_ptr()), self.host.numel(), float(run_seconds),
+                                    C.c_void_p(self.kernel_stream.cuda_stream),
+                                    C.c_void_p(self.side_stream.cuda_stream), C.byref(h)), "csc_queue_create")
+        self._h = h
+
+    def submit(self, beta, Z, lam: float, tol: float, warm_start: bool = False, stream=None) -> int:
+        """Queue one image; beta (K, Z0, Z1) must be complete on `stream` (the
+        current stream by default).  Returns the job index."""
+        import torch
+        _need(beta, torch.float32, "beta")
+        _need(Z, torch.float32, "Z")
+        if self._h is None:
+            raise RuntimeError("queue closed")
+        K, L0, L1 = self.atoms.K, self.atoms.L[0], self.atoms.L[1]
+        if beta.dim() != 3 or beta.shape[0] != K or tuple(Z.shape) != tuple(beta.shape):
+            raise ValueError("beta and Z must both be (K, Z0, Z1)")
+        src = stream if stream is not None else torch.cuda.current_stream(beta.device)
+        self.side_stream.wait_stream(src)
+        T0, T1 = beta.shape[1] + L0 - 1, beta.shape[2] + L1 - 1
+        j = C.c_int(-1)
+        _check(load().csc_queue_submit(self._h, int(T0), int(T1), _ptr(beta), _ptr(Z), float(lam),
+                                       float(tol), int(bool(warm_start)), C.byref(j)), "csc_queue_submit")
+        self._jobs[j.value] = (beta, Z)  # keep the buffers alive while the kernel uses them
+        return j.value
+
+    def poll(self, job: int):
+        """The job's statistics once it has completed, else None (no CUDA call)."""
+        st = SolveStats()
+        rc = load().csc_queue_poll(self._h, int(job), C.byref(st))
+        if rc < 0:
+            raise CscError(-rc, "csc_queue_poll")
+        if rc == 0:
+            return None
+        self._jobs.pop(int(job), None)
+        return st.as_dict()
+
+    def inspect(self, job: int) -> dict:
+        """Device-side state of a job (csc_queue_inspect), for a stalled queue."""
+        out = (C.c_longlong * 8)()
+        _check(load().csc_queue_inspect(self._h, int(job), out), "csc_queue_inspect")
+        keys = ("prefix", "W", "claimed", "done", "njobs", "next_slot", "grid", "complete")
+        return dict(zip(keys, list(out)))
+
+    def wait(self, job: int, timeout: float = 60.0):
+        import time
+        t_end = time.monotonic() + timeout
+        while True:
+            r = self.poll(job)
+            if r is not None:
+                return r
+            if time.monotonic() > t_end:
+                raise TimeoutError(f"queue job {job} did not complete in {timeout} s: {self.inspect(job)}")
+            time.sleep(20e-6)
+
+    def close(self):
+        if self._h is not None:
+            h, self._h = self._h, None
+            _check(load().csc_queue_close(h), "csc_queue_close")
+            self._jobs.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def cdl_dict_stats(Z, X, D_shape, phi=None, psi=None, ws=None, stream=None):

@@ -223,6 +223,16 @@ int launch_corr_refresh(const Geom &g, const real *R, const real *D, const real 
                         unsigned long long *maxdz_bits, cudaStream_t st);
 template <typename real>
 int launch_dtd(const Geom &g, const real *D, real *dtd, cudaStream_t st);
+
+// Load the FP32 kernels of beta-init / refresh / objective (and the tensor-core
+// beta-init) into the context now.  With lazy module loading a kernel is
+// loaded on its first launch, and that load may wait for the kernels already
+// running: a first launch beside a persistent kernel would then stall until
+// the persistent kernel ends.
+int preload_corr_kernels();
+int preload_residual_kernels();
+int preload_umma_kernels();
+int preload_functions(const void *const *fns, int n);
 template <typename real>
 int launch_atom_norms(const Geom &g, const real *D, double *nrm, double *dmax, cudaStream_t st);
 

@@ -237,6 +237,27 @@ int launch_atom_norms(const Geom &g, const real *D, double *nrm, double *dmax, c
     return CSC_OK;
 }
 
+int preload_functions(const void *const *fns, int n) {
+    for (int i = 0; i < n; i++) {
+        cudaFuncAttributes fa;
+        const cudaError_t e = cudaFuncGetAttributes(&fa, fns[i]);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    return CSC_OK;
+}
+
+int preload_corr_kernels() {
+    const void *fns[] = {
+        (const void *)corr_kernel<float, 256, 8, 4, 8, EPI_INIT>,
+        (const void *)corr_kernel<float, 256, 1, 4, 8, EPI_INIT>,
+        (const void *)corr_kernel<float, 256, 8, 4, 8, EPI_REFRESH>,
+        (const void *)corr_kernel<float, 256, 1, 4, 8, EPI_REFRESH>,
+        (const void *)dtd_kernel<float, 256>,
+        (const void *)atom_norm_kernel<float, 256>,
+    };
+    return preload_functions(fns, (int)(sizeof(fns) / sizeof(fns[0])));
+}
+
 #define CSC_INST(real)                                                                         \
     template int launch_corr_init<real>(const Geom &, const real *, const real *, real *,     \
                                         unsigned long long *, cudaStream_t);                  \

@@ -43,9 +43,13 @@ struct UmmaCorrArgs {
     unsigned long long spin_limit;
 };
 
-constexpr int kUmmaBuilders = 256;                 // warps 0-7: operand builders and epilogue
-constexpr int kUmmaThreads = kUmmaBuilders + 32;   // warp 8: MMA issuer
+// Eight warps, so that at most two sit on one SM sub-partition (each of the
+// four has a quarter of the register file): the kernel then still fits beside
+// a persistent kernel that holds half of every sub-partition's registers.
+constexpr int kUmmaBuilders = 224;                 // warps 0-6: operand builders
+constexpr int kUmmaThreads = kUmmaBuilders + 32;   // warp 7: MMA issuer
 constexpr int kUmmaIssuer = kUmmaBuilders / 32;
+constexpr int kUmmaEpi = 128;                      // warps 0-3: epilogue (one per TMEM lane quarter)
 constexpr int kUmmaMaxStages = 4;
 // Core matrices of the A operand are 144 bytes apart (128 + 16): the 32 lanes
 // that each write a 16-byte row of their own core then hit every bank group
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) corr_umma_kernel(UmmaCorrArgs
                          : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
                              (uint32_t)__cvta_generic_to_shared(&accempty[i])),
-                         "r"(kUmmaBuilders)
+                         "r"(kUmmaEpi)
                          : "memory");
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -216,14 +220,15 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) corr_umma_kernel(UmmaCorrArgs
         float lmax = 0.f;
         int seq = 0;
         auto epilogue = [&](int i) -> bool {
+            if (warp >= kUmmaEpi / 32) return true;
             const int tile = (int)blockIdx.x + i * (int)gridDim.x;
             const int s0 = tile / a.tiles_row, s1_0 = (tile % a.tiles_row) * 128, acc = i & 1;
             if (!mbar_wait((uint32_t)__cvta_generic_to_shared(&accfull[acc]), (i >> 1) & 1, a.spin_limit, abort))
                 return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int quarter = warp & 3, half = warp >> 2;
+            const int quarter = warp;
             const int m = 32 * quarter + lane, s1 = s1_0 + m;
-            for (int n0 = 16 * half; n0 < a.Np; n0 += 32) {
+            for (int n0 = 0; n0 < a.Np; n0 += 16) {
                 uint32_t v[16], w[16];
                 const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * acc_cols + n0);
                 asm volatile(
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) corr_umma_kernel(UmmaCorrArgs
             mbar_arrive((uint32_t)__cvta_generic_to_shared(&accempty[acc]));
             return true;
         };
-        // the core matrix this thread builds in a chunk (at most one: CH NC <= 256)
+        // the core matrix this thread builds in a chunk (at most one: CH NC <= 224)
         // comes from X_p[s0 + tau0][col0 .. col0 + 15], col0 = s1_0 + 8 cc; rows
         // rr = 0..7 hold elements rr .. rr + 7.  The values of the next chunk's
         // core are loaded before waiting for its stage.
@@ -363,6 +368,32 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) corr_umma_kernel(UmmaCorrArgs
                      : "memory");
 }
 
+// The dynamic shared-memory limit of the kernel, raised once to the device's
+// opt-in maximum (the launch still asks only for what its plan needs).  Set
+// before a persistent kernel starts, so that no attribute call is made while
+// it runs.
+static int umma_set_smem_limit() {
+    static int done_dev = -1;
+    int dev = 0, optin = 0;
+    CSC_CUDA(cudaGetDevice(&dev));
+    if (done_dev == dev) return CSC_OK;
+    CSC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    CSC_CUDA(cudaFuncGetAttributes(&fa, (const void *)corr_umma_kernel));
+    CSC_CUDA(cudaFuncSetAttribute(corr_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes));
+    CSC_CUDA(cudaFuncSetAttribute(corr_umma_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
+    done_dev = dev;
+    return CSC_OK;
+}
+
+int preload_umma_kernels() {
+    const void *fns[] = {(const void *)corr_umma_kernel};
+    const int rc = preload_functions(fns, 1);
+    return rc ? rc : umma_set_smem_limit();
+}
+
 }  // namespace csc
 
 using namespace csc;
@@ -434,7 +465,7 @@ extern "C" int csc_init_beta_bf16x3(const csc_shape *shape, const float *X, cons
     a.spin_limit = 1ull << 24;
     CSC_CUDA(cudaMemsetAsync(&h->lmax_bits, 0, sizeof(h->lmax_bits), st));
     CSC_CUDA(cudaMemsetAsync(&h->overflow, 0, sizeof(int), st));
-    CSC_CUDA(cudaFuncSetAttribute(corr_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if ((rc = umma_set_smem_limit())) return rc;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -371,6 +371,16 @@ __device__ __forceinline__ unsigned warp_argmax_key(double a, unsigned key) {
     return a < 0.0 ? 0xffffffffu : key;
 }
 
+// Tile plan of a solve: a G0 x G1 grid of tiles of t0 x t1 positions,
+// sub-domains of sub0 x sub1, and the dynamic shared memory of one tile.
+struct Plan {
+    int G0, G1, t0, t1, sub0, sub1;
+    size_t smem;
+};
+// Plan for tiles kept in global memory: tiles of at least 2 L_i (or the
+// caller's tile, at least L_i), at most max_w tiles, squarish in 2-D.
+int make_plan_global(const Geom &g, const csc_solve_opts &o, long long max_w, int rs, Plan *pl);
+
 // Shared-memory tiles, ASYNC and NOLOCK modes (lgcd_async.cu): 8 compute
 // warps and one communication warp.
 constexpr int kAsyncCompute = 256;

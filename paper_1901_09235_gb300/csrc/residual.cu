@@ -154,6 +154,18 @@ int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const re
     return CSC_OK;
 }
 
+int preload_residual_kernels() {
+    const void *fns[] = {
+        (const void *)refresh_reset_kernel,
+        (const void *)compact_any_kernel<float, 256>,
+        (const void *)residual_init_kernel<float>,
+        (const void *)scatter_kernel<float, 128>,
+        (const void *)recon_dense_kernel<float>,
+        (const void *)residual_finish_kernel<float, 256>,
+    };
+    return preload_functions(fns, (int)(sizeof(fns) / sizeof(fns[0])));
+}
+
 template int launch_refresh<float>(const Geom &, const WsLayout &, unsigned char *, const float *,
                                    const float *, const float *, float, float *, cudaStream_t);
 template int launch_refresh<double>(const Geom &, const WsLayout &, unsigned char *, const double *,
