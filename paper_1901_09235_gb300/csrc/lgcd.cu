@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(NT, 1) lgcd_phased_kernel(LgcdArgs<real> a) {
 template <typename real>
 __global__ void __launch_bounds__(kGlobThreads, 2) lgcd_global_kernel(LgcdArgs<real> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    global_tile_worker<real, kGlobThreads>(a, blockIdx.x, smem_raw);
+    global_tile_worker<real, kGlobThreads, 6>(a, blockIdx.x, smem_raw);
 }
 
 // Header reset before a launch: pending = number of workers, counters 0.

@@ -20,130 +20,305 @@ namespace csc {
 // yet observed by their tile.  One sub-domain per iteration, scanned and
 // updated by the whole CTA.
 constexpr int kGlobThreads = 512;
+// Boxes of K x rows x cols are walked in units of (atom, block of RB rows,
+// 32-column chunk): a warp takes units NW apart, issues the loads of all rows
+// of its unit, then evaluates them.  Two divisions per unit, none per
+// element.  RB is the largest block a kernel holds in registers without
+// spilling.
 
-template <typename real, int NT>
+template <typename real, int NT, int RB>
 __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char *smem_raw);
+
+// Warp argmax with the oracle's tie-break (larger |dZ|, then smaller key);
+// every lane gets the winner, with its Z' and dZ.
+template <typename real>
+__device__ __forceinline__ Cand<real> warp_argmax(const Cand<real> &c) {
+    real am = c.a;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+    unsigned km = c.a == am ? c.key : 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) km = min(km, __shfl_xor_sync(0xffffffffu, km, o));
+    const unsigned who = __ballot_sync(0xffffffffu, c.a == am && c.key == km);
+    const int src = who ? __ffs(who) - 1 : 0;
+    Cand<real> r;
+    r.a = am;
+    r.key = km;
+    r.znew = __shfl_sync(0xffffffffu, c.znew, src);
+    r.dz = __shfl_sync(0xffffffffu, c.dz, src);
+    return r;
+}
 
 // The worker of tile w (all NT threads of the CTA); smem_raw holds at least
 // 2 K elements.  Returns when the solve of `a` ends.
-template <typename real, int NT>
+//
+// One sub-domain per iteration.  Barriers per iteration: one after the scan
+// (per-warp argmax partials, double-buffered by iteration parity, with the
+// flag / stop state read by thread 0 while it scanned), one after the
+// soft-lock maxima (border candidates only) and one after the window update
+// (accepted candidates only).
+template <typename real, int NT, int RB>
 __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char *smem_raw) {
+    constexpr int kRowBlock = RB;
+    constexpr int NW = NT / 32;
     real *snrm = reinterpret_cast<real *>(smem_raw), *sinv = snrm + a.K;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ta = w / a.G1, tb = w % a.G1;
     const int or0 = ta * a.t0, oc0 = tb * a.t1;
     const int h = min(a.t0, a.Z0 - or0), wd = min(a.t1, a.Z1 - oc0);
     const int ns0 = (h + a.sub0 - 1) / a.sub0, ns1 = (wd + a.sub1 - 1) / a.sub1, M = ns0 * ns1;
-    const int K = a.K, WW = a.W0 * a.W1;
+    const int K = a.K;
     const size_t plane = (size_t)a.Z0 * a.Z1;
     for (int k = threadIdx.x; k < K; k += NT) {
         snrm[k] = real(a.nrm[k]);
         sinv[k] = real(1.0 / a.nrm[k]);
     }
     int *flag = a.ctl + (size_t)w * kDirs * 32;  // this tile's counter
-    __shared__ int s_ctl[4];                     // new flag bumps, state, accept
-    __shared__ Cand<real> s_best;
-    long long n_upd = 0, n_it = 0, n_rej = 0, n_sub = 0, n_msg = 0;
-    const unsigned long long deadline = globaltimer_ns() + a.timeout_ns;
-    real guard = real(0);
-    if (a.guard_on) {
-        double g = 1e300;
-        for (int k = 0; k < K; k++) g = fmin(g, 50.0 / a.dmax[k]);
-        guard = real(g);
+    __shared__ Cand<real> s_red[2][NW];          // per-warp argmax, by iteration parity
+    __shared__ int s_ctl[2][2];                  // flag bumps seen, stop state
+    __shared__ real s_lo[NW], s_hi[NW];          // soft-lock maxima per warp
+    __shared__ int s_pause;
+    // state only thread 0 uses, kept out of every thread's registers
+    __shared__ unsigned long long s_deadline;
+    __shared__ real s_guard;
+    __shared__ int s_seen, s_cnt[5];  // updates, iterations, rejected, below tol, messages
+    // SM cycles of thread 0 per phase: scan, wait for the scan barrier,
+    // soft-lock, window update, update barrier and flags, pause
+    __shared__ unsigned long long s_ph[6], s_t;
+    if (threadIdx.x == 0) {
+        s_deadline = globaltimer_ns() + a.timeout_ns;
+        real guard = real(0);
+        if (a.guard_on) {
+            double g = 1e300;
+            for (int k = 0; k < K; k++) g = fmin(g, 50.0 / a.dmax[k]);
+            guard = real(g);
+        }
+        s_guard = guard;
+        s_seen = 0;
+        for (int i = 0; i < 5; i++) s_cnt[i] = 0;
+        for (int i = 0; i < 6; i++) s_ph[i] = 0;
+        s_t = clock64();
     }
-    int seen = 0, m = 0, quiet = 0;
+    // Dirty sub-domains (tiles of at most 64): a bit is cleared when a scan
+    // finds nothing above tol and set again when beta in the sub-domain may
+    // have changed -- an accepted update whose window V(s0) reaches it, or a
+    // neighbour's flag bump for those along the border band.  The worker
+    // pauses once no sub-domain is dirty.  Larger tiles scan cyclically and
+    // pause after M quiet iterations.
+    const bool use_mask = M <= 64;
+    unsigned long long dmask = 0, ring = 0;
+    if (use_mask) {
+        dmask = M == 64 ? ~0ull : ((1ull << M) - 1ull);
+        for (int q = 0; q < M; q++) {
+            const int qr = q / ns1, qc = q - qr * ns1;
+            const int rr0 = qr * a.sub0, rr1 = min(h, rr0 + a.sub0), cc0 = qc * a.sub1, cc1 = min(wd, cc0 + a.sub1);
+            if (rr0 < a.L0 - 1 || rr1 > h - (a.L0 - 1) || cc0 < a.L1 - 1 || cc1 > wd - (a.L1 - 1))
+                ring |= 1ull << q;
+        }
+    }
+    int m = 0, quiet = 0, par = 0;
     __syncthreads();
     for (;;) {
+        // thread 0 reads this tile's flag counter and the stop word; the loads
+        // overlap its share of the scan
+        int f_now = 0, stop_now = 0;
         if (threadIdx.x == 0) {
+            f_now = ld_relaxed(flag);
+            stop_now = ld_relaxed(&a.hdr->stop);
+        }
+        // ---- scan sub-domain m (Eq. gcd_candidate)
+        const int mr = m / ns1, mc = m - mr * ns1;
+        const int r0 = mr * a.sub0, c0 = mc * a.sub1;
+        const int bh = min(a.sub0, h - r0), bw = min(a.sub1, wd - c0);
+        Cand<real> c{real(-1), 0xffffffffu, real(0), real(0)};
+        {
+            const int nrb = (bh + kRowBlock - 1) / kRowBlock, nch = (bw + 31) >> 5, per_k = nrb * nch;
+            for (int u = warp; u < K * per_k; u += NW) {
+                const int k = u / per_k, rem = u - k * per_k, rb = rem / nch, ch = rem - rb * nch;
+                const int cc = ch * 32 + lane, lj = c0 + cc, li = r0 + rb * kRowBlock;
+                const int nrow = cc < bw ? min(kRowBlock, bh - rb * kRowBlock) : 0;
+                // positions are below 2^31: 32-bit offsets within atom k's plane
+                const real *bk = a.beta + (size_t)k * plane, *zk = a.Z + (size_t)k * plane;
+                const int o0 = (or0 + li) * a.Z1 + oc0 + lj;
+                real bv[kRowBlock], zv[kRowBlock];
+#pragma unroll
+                for (int q = 0; q < kRowBlock; q++) {
+                    if (q < nrow) {
+                        bv[q] = __ldcg(bk + (o0 + q * a.Z1));
+                        // Z through L2: in the persistent queue an L1 line may
+                        // still hold this address from an earlier job
+                        zv[q] = __ldcg(zk + (o0 + q * a.Z1));
+                    }
+                }
+                const real nk = snrm[k], ik = sinv[k];
+#pragma unroll
+                for (int q = 0; q < kRowBlock; q++) {
+                    if (q < nrow) {
+                        const real zn = coord_update(bv[q], a.lambda, nk, ik);
+                        const real dz = zn - zv[q];
+                        Cand<real> x{dz < real(0) ? -dz : dz, (unsigned)(((li + q) * a.t1 + lj) * K + k), zn, dz};
+                        if (better(x, c)) c = x;
+                    }
+                }
+            }
+        }
+        c = warp_argmax(c);
+        if (threadIdx.x == 0) {
+            const unsigned long long t = clock64();
+            s_ph[0] += t - s_t;
+            s_t = t;
             int got = 0, state = 0;
-            const int f = ld_relaxed(flag);
-            if (f != seen) {
-                got = f - seen;
-                seen = f;
+            if (f_now != s_seen) {
+                got = f_now - s_seen;
+                s_seen = f_now;
                 atomicSub(&a.hdr->pending, got);  // observed: no longer in flight
             }
-            if (ld_relaxed(&a.hdr->stop)) state = 1;
-            else if (globaltimer_ns() > deadline) {
+            if (stop_now) state = 1;
+            else if (globaltimer_ns() > s_deadline) {
                 set_stop(a.hdr, CSC_ERR_TIMEOUT);
                 state = 1;
             }
-            s_ctl[0] = got;
-            s_ctl[1] = state;
+            s_ctl[par][0] = got;
+            s_ctl[par][1] = state;
         }
+        if (lane == 0) s_red[par][warp] = c;
         __syncthreads();
-        if (s_ctl[1]) break;
-        const int got = s_ctl[0];
-        // ---- scan sub-domain m (Eq. gcd_candidate)
-        const int mr = m / ns1, mc = m % ns1;
-        const int r0 = mr * a.sub0, c0 = mc * a.sub1;
-        const int bh = min(a.sub0, h - r0), bw = min(a.sub1, wd - c0), nb = bh * bw;
-        Cand<real> c{real(-1), 0xffffffffu, real(0), real(0)};
-        for (int q = threadIdx.x; q < K * nb; q += NT) {
-            const int k = q / nb, r = q % nb, li = r0 + r / bw, lj = c0 + r % bw;
-            const size_t g = k * plane + (size_t)(or0 + li) * a.Z1 + oc0 + lj;
-            const real zn = coord_update(__ldcg(a.beta + g), a.lambda, snrm[k], sinv[k]);
-            // Z through L2: in the persistent queue an L1 line may still hold
-            // this address from an earlier job whose buffer was recycled
-            const real dz = zn - __ldcg(a.Z + g);
-            Cand<real> x{dz < real(0) ? -dz : dz, (unsigned)((li * a.t1 + lj) * K + k), zn, dz};
-            if (better(x, c)) c = x;
+        if (s_ctl[par][1]) break;
+        const int got = s_ctl[par][0];
+        Cand<real> best = s_red[par][0];
+#pragma unroll 4
+        for (int i = 1; i < NW; i++) {
+            const Cand<real> y = s_red[par][i];
+            if (better(y, best)) best = y;
         }
-        const Cand<real> best = block_argmax<real, NT>(c);
-        n_it++;
+        par ^= 1;
+        if (threadIdx.x == 0) {
+            s_cnt[1]++;
+            const unsigned long long t = clock64();
+            s_ph[1] += t - s_t;
+            s_t = t;
+        }
         const bool active = best.a >= a.eps;
+        bool accepted = false;
+        int li0 = 0, lj0 = 0;
         if (active) {
             const unsigned pos = best.key / (unsigned)K;
-            const int k0 = (int)(best.key % (unsigned)K);
-            const int li0 = (int)(pos / (unsigned)a.t1), lj0 = (int)(pos % (unsigned)a.t1);
+            const int k0 = (int)(best.key - pos * (unsigned)K);
+            li0 = (int)(pos / (unsigned)a.t1);
+            lj0 = (int)(pos - (unsigned)li0 * (unsigned)a.t1);
             const int gi0 = or0 + li0, gj0 = oc0 + lj0;
             const bool border = in_band(li0, lj0, h, wd, a.L0, a.L1);
             bool accept = true;
             if (border && a.mode == CSC_MODE_ASYNC) {
-                // soft-lock over the part of V(s0) outside the tile: at most one
-                // strip of rows outside the tile rows (full width of V) and one
-                // strip of columns outside the tile columns (tile rows only)
+                // soft-lock over the part of V(s0) outside the tile: strip A =
+                // rows outside the tile rows (full width of V), strip B = tile
+                // rows, columns outside the tile columns
                 const int v0 = max(0, gi0 - (a.L0 - 1)), v1 = min(a.Z0, gi0 + a.L0);
                 const int u0 = max(0, gj0 - (a.L1 - 1)), u1 = min(a.Z1, gj0 + a.L1);
                 const int ra0 = v0 < or0 ? v0 : max(v0, or0 + h), ra1 = v0 < or0 ? min(v1, or0) : v1;
                 const int rb0 = max(v0, or0), rb1 = min(v1, or0 + h);
                 const int cb0 = u0 < oc0 ? u0 : max(u0, oc0 + wd), cb1 = u0 < oc0 ? min(u1, oc0) : u1;
-                const int n1 = max(0, ra1 - ra0) * (u1 - u0), n2 = max(0, rb1 - rb0) * max(0, cb1 - cb0);
+                const int nA = max(0, ra1 - ra0), nB = (cb1 > cb0) ? max(0, rb1 - rb0) : 0;
+                const int wA = u1 - u0, wB = max(0, cb1 - cb0);
                 real lo = real(-1), hi = real(-1);
-                for (int q = threadIdx.x; q < K * (n1 + n2); q += NT) {
-                    const int k = q / (n1 + n2), e = q % (n1 + n2);
-                    int gi, gj;
-                    if (e < n1) {
-                        gi = ra0 + e / (u1 - u0);
-                        gj = u0 + e % (u1 - u0);
-                    } else {
-                        gi = rb0 + (e - n1) / (cb1 - cb0);
-                        gj = cb0 + (e - n1) % (cb1 - cb0);
+                const int nchA = (wA + 31) >> 5, nchB = (wB + 31) >> 5;
+                const int unA = ((nA + kRowBlock - 1) / kRowBlock) * nchA;
+                const int per_k = unA + ((nB + kRowBlock - 1) / kRowBlock) * nchB;
+                for (int u = warp; u < K * per_k; u += NW) {
+                    const int k = u / per_k, rem = u - k * per_k;
+                    const bool inA = rem < unA;
+                    const int nchS = inA ? nchA : nchB, remS = inA ? rem : rem - unA;
+                    const int rb = remS / nchS, ch = remS - rb * nchS;
+                    const int cc = ch * 32 + lane;
+                    const int gi = (inA ? ra0 : rb0) + rb * kRowBlock, gj = (inA ? u0 : cb0) + cc;
+                    const int nrow = cc < (inA ? wA : wB) ? min(kRowBlock, (inA ? nA : nB) - rb * kRowBlock) : 0;
+                    const real *bk = a.beta + (size_t)k * plane, *zk = a.Z + (size_t)k * plane;
+                    const int o0 = gi * a.Z1 + gj;
+                    real bv[kRowBlock], zv[kRowBlock];
+#pragma unroll
+                    for (int q = 0; q < kRowBlock; q++) {
+                        if (q < nrow) {
+                            bv[q] = ld_relaxed(bk + (o0 + q * a.Z1));
+                            zv[q] = ld_relaxed(zk + (o0 + q * a.Z1));
+                        }
                     }
-                    const size_t g = k * plane + (size_t)gi * a.Z1 + gj;
-                    real d = coord_update(ld_relaxed(a.beta + g), a.lambda, snrm[k], sinv[k]) - ld_relaxed(a.Z + g);
-                    d = d < real(0) ? -d : d;
-                    if ((gi / a.t0) * a.G1 + gj / a.t1 < w) lo = max(lo, d);
-                    else hi = max(hi, d);
+                    // rank of the tile holding (gi + q, gj): neighbours of a
+                    // tile are at most one tile away in each direction
+                    const int tj = gj < oc0 ? tb - 1 : (gj >= oc0 + wd ? tb + 1 : tb);
+                    const real nk = snrm[k], ik = sinv[k];
+#pragma unroll
+                    for (int q = 0; q < kRowBlock; q++) {
+                        if (q < nrow) {
+                            real d = coord_update(bv[q], a.lambda, nk, ik) - zv[q];
+                            d = d < real(0) ? -d : d;
+                            const int gq = gi + q;
+                            const int ti = gq < or0 ? ta - 1 : (gq >= or0 + h ? ta + 1 : ta);
+                            if (ti * a.G1 + tj < w) lo = max(lo, d);
+                            else hi = max(hi, d);
+                        }
+                    }
                 }
-                real mhi;
-                const real mlo = block_max2<real, NT>(lo, hi, &mhi);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                }
+                if (lane == 0) {
+                    s_lo[warp] = lo;
+                    s_hi[warp] = hi;
+                }
+                __syncthreads();
+                real mlo = s_lo[0], mhi = s_hi[0];
+#pragma unroll 4
+                for (int i = 1; i < NW; i++) {
+                    mlo = max(mlo, s_lo[i]);
+                    mhi = max(mhi, s_hi[i]);
+                }
                 accept = best.a > mlo && best.a >= mhi;
-                if (!accept) n_rej += threadIdx.x == 0;
+                if (threadIdx.x == 0) {
+                    if (!accept) s_cnt[2]++;
+                    const unsigned long long t = clock64();
+                    s_ph[2] += t - s_t;
+                    s_t = t;
+                }
             }
             if (accept) {
-                // beta_k[s] -= C[k][k0][s - s0] dz on V(s0) within the domain
+                accepted = true;
+                // Z first: the barrier after the window update publishes both
+                // to the next scan
+                if (threadIdx.x == 0) a.Z[k0 * plane + (size_t)gi0 * a.Z1 + gj0] = best.znew;
+                // beta_k[s] -= C[k][k0][s - s0] dz on V(s0) within the domain:
+                // the table loads of a unit first, then its reductions
                 const real dz = best.dz;
-                for (int q = threadIdx.x; q < K * WW; q += NT) {
-                    const int k = q / WW, r = q % WW;
-                    const int gi = gi0 + r / a.W1 - (a.L0 - 1), gj = gj0 + r % a.W1 - (a.L1 - 1);
-                    if (gi < 0 || gi >= a.Z0 || gj < 0 || gj >= a.Z1) continue;
-                    if (k == k0 && gi == gi0 && gj == gj0) continue;
-                    const real cval = __ldg(a.dtd + ((size_t)k * K + k0) * WW + r);
-                    atomicAdd(a.beta + k * plane + (size_t)gi * a.Z1 + gj, -(cval * dz));
+                const int W0 = a.W0, W1 = a.W1;
+                const int nrb = (W0 + kRowBlock - 1) / kRowBlock, nch = (W1 + 31) >> 5, per_k = nrb * nch;
+                for (int u = warp; u < K * per_k; u += NW) {
+                    const int k = u / per_k, rem = u - k * per_k, rb = rem / nch, ch = rem - rb * nch;
+                    const int cw = ch * 32 + lane, rw0 = rb * kRowBlock;
+                    const int gj = gj0 + cw - (a.L1 - 1), gi = gi0 + rw0 - (a.L0 - 1);
+                    // rows of this unit inside the domain: [q_lo, q_hi)
+                    const bool colok = cw < W1 && gj >= 0 && gj < a.Z1;
+                    const int q_lo = max(0, -gi), q_hi = colok ? min(min(kRowBlock, W0 - rw0), a.Z0 - gi) : 0;
+                    const real *crow = a.dtd + (((size_t)k * K + k0) * W0 + rw0) * W1 + cw;
+                    real cv[kRowBlock];
+#pragma unroll
+                    for (int q = 0; q < kRowBlock; q++)
+                        if (q >= q_lo && q < q_hi) cv[q] = __ldg(crow + q * W1);
+                    real *bk = a.beta + (size_t)k * plane;
+                    const int o0 = gi * a.Z1 + gj;
+#pragma unroll
+                    for (int q = 0; q < kRowBlock; q++)
+                        if (q >= q_lo && q < q_hi && !(k == k0 && gi + q == gi0 && gj == gj0))
+                            atomicAdd(bk + (o0 + q * a.Z1), -(cv[q] * dz));
+                }
+                if (threadIdx.x == 0) {
+                    const unsigned long long t = clock64();
+                    s_ph[3] += t - s_t;
+                    s_t = t;
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    a.Z[k0 * plane + (size_t)gi0 * a.Z1 + gj0] = best.znew;
-                    n_upd++;
+                    s_cnt[0]++;
                     int dl[kDirs];
                     Tile<real, NT> tt;
                     tt.ta = ta;
@@ -159,29 +334,45 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                             dir_offset(dl[i], dr, dc);
                             atomicAdd(a.ctl + (size_t)((ta + dr) * a.G1 + (tb + dc)) * kDirs * 32, 1);
                         }
-                        n_msg += nd;
+                        s_cnt[4] += nd;
                     }
                     if (a.max_updates > 0) {
                         unsigned long long prev = atomicAdd(&a.hdr->updates_total, 1ull);
                         if ((long long)prev + 1 >= a.max_updates) set_stop(a.hdr, CSC_NOT_CONVERGED);
                     }
                     const real az = best.znew < real(0) ? -best.znew : best.znew;
-                    if (a.guard_on && az > guard) set_stop(a.hdr, CSC_ERR_DIVERGED);
+                    if (a.guard_on && az > s_guard) set_stop(a.hdr, CSC_ERR_DIVERGED);
+                    const unsigned long long t = clock64();
+                    s_ph[4] += t - s_t;
+                    s_t = t;
                 }
             }
-        } else {
-            n_sub++;
+        } else if (threadIdx.x == 0) {
+            s_cnt[3]++;
         }
-        quiet = (active || got > 0) ? 0 : quiet + 1;
-        m = (m + 1 == M) ? 0 : m + 1;
-        __syncthreads();
-        if (quiet >= M) {
+        bool pause;
+        if (use_mask) {
+            if (!active) dmask &= ~(1ull << m);
+            if (accepted) {
+                // sub-domains that V(s0) reaches (rows / columns within L - 1)
+                const int qr0 = max(0, li0 - (a.L0 - 1)) / a.sub0, qr1 = min(h - 1, li0 + a.L0 - 1) / a.sub0;
+                const int qc0 = max(0, lj0 - (a.L1 - 1)) / a.sub1, qc1 = min(wd - 1, lj0 + a.L1 - 1) / a.sub1;
+                for (int qr = qr0; qr <= qr1; qr++)
+                    for (int qc = qc0; qc <= qc1; qc++) dmask |= 1ull << (qr * ns1 + qc);
+            }
+            if (got > 0) dmask |= ring;
+            pause = dmask == 0;
+        } else {
+            quiet = (active || got > 0) ? 0 : quiet + 1;
+            pause = quiet >= M;
+        }
+        if (pause) {
             // pause until a neighbour bumps the flag or every worker is done
             if (threadIdx.x == 0) {
                 atomicSub(&a.hdr->pending, 1);
                 int state = 0;
                 for (;;) {
-                    if (ld_relaxed(flag) != seen) {
+                    if (ld_relaxed(flag) != s_seen) {
                         atomicAdd(&a.hdr->pending, 1);
                         break;
                     }
@@ -189,28 +380,45 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                         state = 1;
                         break;
                     }
-                    if (globaltimer_ns() > deadline) {
+                    if (globaltimer_ns() > s_deadline) {
                         set_stop(a.hdr, CSC_ERR_TIMEOUT);
                         state = 1;
                         break;
                     }
                     __nanosleep(256);
                 }
-                s_ctl[2] = state;
+                s_pause = state;
+                const unsigned long long t = clock64();
+                s_ph[5] += t - s_t;
+                s_t = t;
             }
             __syncthreads();
-            if (s_ctl[2]) break;
+            if (s_pause) break;
             quiet = 0;
+            // woken by a flag bump: beta along the border band has changed
+            dmask |= ring;
+            if (use_mask && dmask == 0) dmask = M == 64 ? ~0ull : ((1ull << M) - 1ull);
+        }
+        if (use_mask) {
+            // the next dirty sub-domain after m, cyclically
+            const unsigned long long above = m + 1 < 64 ? (dmask >> (m + 1)) << (m + 1) : 0ull;
+            m = above ? __ffsll((long long)above) - 1 : __ffsll((long long)dmask) - 1;
+        } else {
+            m = (m + 1 == M) ? 0 : m + 1;
         }
     }
     if (threadIdx.x == 0) {
-        atomicAdd((unsigned long long *)&a.hdr->stat[ST_UPDATES], (unsigned long long)n_upd);
-        atomicAdd((unsigned long long *)&a.hdr->stat[ST_ITERS], (unsigned long long)n_it);
-        atomicAdd((unsigned long long *)&a.hdr->stat[ST_REJECTED], (unsigned long long)n_rej);
-        atomicAdd((unsigned long long *)&a.hdr->stat[ST_SUBTOL], (unsigned long long)n_sub);
-        atomicAdd((unsigned long long *)&a.hdr->stat[ST_MESSAGES], (unsigned long long)n_msg);
-        atomicMax(&a.hdr->wmax[0], (unsigned long long)n_it);
-        atomicMax(&a.hdr->wmax[1], (unsigned long long)n_upd);
+        atomicAdd((unsigned long long *)&a.hdr->stat[ST_UPDATES], (unsigned long long)s_cnt[0]);
+        atomicAdd((unsigned long long *)&a.hdr->stat[ST_ITERS], (unsigned long long)s_cnt[1]);
+        atomicAdd((unsigned long long *)&a.hdr->stat[ST_REJECTED], (unsigned long long)s_cnt[2]);
+        atomicAdd((unsigned long long *)&a.hdr->stat[ST_SUBTOL], (unsigned long long)s_cnt[3]);
+        atomicAdd((unsigned long long *)&a.hdr->stat[ST_MESSAGES], (unsigned long long)s_cnt[4]);
+        atomicMax(&a.hdr->wmax[0], (unsigned long long)s_cnt[1]);
+        atomicMax(&a.hdr->wmax[1], (unsigned long long)s_cnt[0]);
+        for (int i = 0; i < 6; i++) {
+            atomicAdd(&a.hdr->tph[i], s_ph[i]);
+            atomicMax(&a.hdr->tphmax[i], s_ph[i]);
+        }
     }
 }
 

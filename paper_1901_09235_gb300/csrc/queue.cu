@@ -50,7 +50,7 @@ struct QueueHostSlot {  // pinned host memory, one per job
     unsigned long long t_start;
 };
 
-// Two CTAs of 256 threads (at most 64 registers a thread) per SM: the
+// Two CTAs of 256 threads (at most 72 registers a thread) per SM: the
 // persistent grid leaves half of every SM's registers, most of its threads and
 // nearly all of its shared memory to the beta-init and refresh kernels of the
 // other streams.
@@ -72,7 +72,10 @@ __device__ __forceinline__ void st_release_sys(int *p, int v) {
     asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kQueueThreads, 4) lgcd_queue_kernel(QueueCtl *qc, QueueJob *jobs, int max_jobs,
+// At most 72 registers a thread: two CTAs then hold 9,216 of the 16,384
+// registers of each SM sub-partition, leaving room for the tensor-core
+// beta-init (two warps of at most 104 registers each per sub-partition).
+__global__ void __maxnreg__(72) lgcd_queue_kernel(QueueCtl *qc, QueueJob *jobs, int max_jobs,
                                                                       QueueHostSlot *host,
                                                                       unsigned long long run_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kQueueThreads, 4) lgcd_queue_kernel(QueueCtl *
         const int j = s_job;
         stage_l2(&s_args, &jobs[j].a);
         __syncthreads();
-        global_tile_worker<float, kQueueThreads>(s_args, s_tile, smem_raw);
+        global_tile_worker<float, kQueueThreads, 4>(s_args, s_tile, smem_raw);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();

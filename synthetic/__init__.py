@@ -113,6 +113,34 @@ def make_problem(w: Workload, seed: int, D: np.ndarray | None = None):
     return X.astype(np.float32), D, Z.astype(np.float32, copy=False)
 
 
+def make_image_device(w: Workload, seed: int, D: np.ndarray, device="cuda"):
+    """A 2-D observation for benchmark inputs too large to build on the host:
+    Z is drawn as in ``make_problem`` (the same sequence from the same seed),
+    and X = Z * D + noise is formed on ``device`` in float32 (a transposed
+    convolution of Z with the atoms, then N(0, sigma^2) from torch's generator
+    seeded from the same stream).  Returns X as a float32 device tensor."""
+    import torch
+    rng = np.random.default_rng(seed)
+    if len(w.T) != 2:
+        raise ValueError("2-D workloads only")
+    Tz = tuple(t - l + 1 for t, l in zip(w.T, w.L))
+    n = int(np.prod(Tz))
+    Zd = torch.zeros((w.K, n), dtype=torch.float32, device=device)
+    for k in range(w.K):
+        cnt = int(rng.binomial(n, w.density))
+        pos = rng.choice(n, size=cnt, replace=False)
+        amp = rng.standard_normal(cnt)
+        if w.nonneg:
+            amp = np.abs(amp)
+        Zd[k, torch.from_numpy(pos).to(device)] = torch.from_numpy(amp.astype(np.float32)).to(device)
+    Dd = torch.from_numpy(np.ascontiguousarray(D, dtype=np.float32)).to(device)
+    X = torch.nn.functional.conv_transpose2d(Zd.view((1, w.K) + Tz), Dd)[0]
+    g = torch.Generator(device=device)
+    g.manual_seed(int(rng.integers(1 << 62)))
+    X += w.sigma * torch.randn(X.shape, generator=g, device=device, dtype=torch.float32)
+    return X.contiguous()
+
+
 def served_sizes(n: int, seed: int, lo: int = 64, hi: int = 2048):
     """Square image sides, log-uniform in [lo, hi], rounded to integers."""
     rng = np.random.default_rng(seed)
