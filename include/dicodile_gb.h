@@ -88,6 +88,9 @@ typedef struct {
     int beta_init;        /* cdl_fit: 0 = beta-init in FP32 (csc_init_beta), 1 = on the
                              tensor cores in split bf16 (csc_init_beta_bf16x3) after the
                              first iteration, whose exact beta also fixes lambda          */
+    double stop_margin;   /* workers stop when no |dZ| reaches stop_margin * tol, in (0, 1]
+                             (0 = 0.99 in FP32, 1 in FP64); the check on a beta
+                             recomputed from scratch always uses tol itself            */
 } csc_solve_opts;
 
 typedef struct {
@@ -268,12 +271,14 @@ CSC_API int csc_queue_create(const csc_shape *atoms, const float *D, const float
  * csc_init_beta, or a consistent warm state with warm_start = 1, in which
  * case Z is kept; otherwise Z is zeroed).  beta and Z belong to the caller and
  * are updated in place until the job completes.  job_out: index for
- * csc_queue_poll.  The image is cut into at most opts.max_workers tiles
- * (default: 7/8 of the grid, so that small jobs start beside a large one).
+ * csc_queue_poll.  opts (may be NULL: the queue's) sets this job's tile and
+ * sub-domain sizes, mode, stop margin and timeout; the image is cut into at
+ * most opts.max_workers tiles (default: 7/8 of the grid, so that small jobs
+ * start beside a large one).
  * CSC_ERR_WORKSPACE when max_jobs or ctl_slots is used up (poll finished
  * jobs to free control slots). */
 CSC_API int csc_queue_submit(csc_queue *queue, int T0, int T1, float *beta, float *Z, float lambda,
-                             float tol, int warm_start, int *job_out);
+                             float tol, int warm_start, const csc_solve_opts *opts, int *job_out);
 
 /* 1 when the job has completed (stats filled: status, updates, iterations,
  * rejected, messages, device time in kernel_ms), 0 while it runs, negative

@@ -34,7 +34,7 @@ class SolveOpts(C.Structure):
                 ("max_workers", C.c_int), ("max_updates", C.c_longlong),
                 ("timeout_s", C.c_double), ("beta_refresh", C.c_int),
                 ("divergence_guard", C.c_int), ("warm_start", C.c_int), ("placement", C.c_int),
-                ("beta_init", C.c_int)]
+                ("beta_init", C.c_int), ("stop_margin", C.c_double)]
 
 
 class SolveStats(C.Structure):
@@ -102,7 +102,7 @@ def load():
         "csc_refresh_beta": (i, [S, p, p, p, C.c_float, p, C.POINTER(d), C.POINTER(d), p, sz, p]),
         "csc_queue_workspace_size": (i, [S, i, i, C.POINTER(sz), C.POINTER(sz)]),
         "csc_queue_create": (i, [S, p, p, O, i, i, p, sz, p, sz, d, p, p, C.POINTER(p)]),
-        "csc_queue_submit": (i, [p, i, i, p, p, C.c_float, C.c_float, i, C.POINTER(i)]),
+        "csc_queue_submit": (i, [p, i, i, p, p, C.c_float, C.c_float, i, O, C.POINTER(i)]),
         "csc_queue_poll": (i, [p, i, ST]),
         "csc_queue_close": (i, [p]),
         "csc_queue_inspect": (i, [p, i, C.POINTER(C.c_longlong)]),
@@ -348,9 +348,11 @@ class Queue:
                                     C.c_void_p(self.side_stream.cuda_stream), C.byref(h)), "csc_queue_create")
         self._h = h
 
-    def submit(self, beta, Z, lam: float, tol: float, warm_start: bool = False, stream=None) -> int:
+    def submit(self, beta, Z, lam: float, tol: float, warm_start: bool = False, stream=None,
+               opts: SolveOpts | None = None) -> int:
         """Queue one image; beta (K, Z0, Z1) must be complete on `stream` (the
-        current stream by default).  Returns the job index."""
+        current stream by default).  opts: this job's solve options (None: the
+        queue's).  Returns the job index."""
         import torch
         _need(beta, torch.float32, "beta")
         _need(Z, torch.float32, "Z")
@@ -364,7 +366,8 @@ class Queue:
         T0, T1 = beta.shape[1] + L0 - 1, beta.shape[2] + L1 - 1
         j = C.c_int(-1)
         _check(load().csc_queue_submit(self._h, int(T0), int(T1), _ptr(beta), _ptr(Z), float(lam),
-                                       float(tol), int(bool(warm_start)), C.byref(j)), "csc_queue_submit")
+                                       float(tol), int(bool(warm_start)), C.byref(opts) if opts else None,
+                                       C.byref(j)), "csc_queue_submit")
         self._jobs[j.value] = (beta, Z)  # keep the buffers alive while the kernel uses them
         return j.value
 

@@ -355,6 +355,7 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     csc_default_opts(&o);
     if (opts_in) o = *opts_in;
     if (o.mode < 0 || o.mode > 2 || o.beta_refresh < 0) return CSC_ERR_INVALID;
+    if (!(o.stop_margin >= 0.0 && o.stop_margin <= 1.0)) return CSC_ERR_INVALID;
     const int rs = (int)sizeof(real);
     if (o.placement < 0 || o.placement > 2) return CSC_ERR_INVALID;
     bool global = o.placement == 2;
@@ -461,7 +462,8 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     // FP32 solves stop at 0.99 tol so that rounding drift of the incrementally
     // maintained beta rarely pushes a coordinate back above tol on the
     // recomputed beta; the FP64 build keeps tol exactly.
-    a.eps = sizeof(real) == 4 ? real(0.99) * tol : tol;
+    const double margin = o.stop_margin > 0.0 ? o.stop_margin : (sizeof(real) == 4 ? 0.99 : 1.0);
+    a.eps = real(margin) * tol;
     a.max_updates = o.max_updates;
     double tmo = o.timeout_s > 0 ? o.timeout_s : 30.0;
     a.timeout_ns = (unsigned long long)(tmo * 1e9);

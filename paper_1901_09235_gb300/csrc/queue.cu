@@ -319,8 +319,10 @@ int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, c
 }
 
 int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float lambda, float tol, int warm_start,
-                     int *job_out) {
+                     const csc_solve_opts *opts, int *job_out) {
     if (!q || !beta || !Z || !job_out || !(lambda >= 0.f) || !(tol > 0.f)) return CSC_ERR_INVALID;
+    const csc_solve_opts o = opts ? *opts : q->opts;
+    if (!(o.stop_margin >= 0.0 && o.stop_margin <= 1.0) || o.mode < 0 || o.mode > 2) return CSC_ERR_INVALID;
     if (q->njobs >= q->max_jobs || q->free_ctl.empty()) return CSC_ERR_WORKSPACE;
     csc_shape s;
     s.d = 2;
@@ -334,7 +336,6 @@ int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float 
     int rc = make_geom(&s, &g);
     if (rc) return rc;
     Plan pl;
-    csc_solve_opts o = q->opts;
     // one job takes at most 7/8 of the grid unless opts.max_workers says
     // otherwise, so that small jobs queued behind a large one start beside it
     rc = make_plan_global(g, o, q->grid - q->grid / 8, 4, &pl);
@@ -374,7 +375,7 @@ int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float 
     a.cap = kMailboxCap;
     a.Mmax = 0;
     a.lambda = lambda;
-    a.eps = 0.99f * tol;  // the FP32 stopping margin of the single solve
+    a.eps = (float)(o.stop_margin > 0.0 ? o.stop_margin : 0.99) * tol;  // as in the single solve
     a.max_updates = 0;
     const double tmo = o.timeout_s > 0 ? o.timeout_s : 30.0;
     a.timeout_ns = (unsigned long long)(tmo * 1e9);

@@ -122,7 +122,7 @@ class Server:
 
     def __init__(self, D, hbm_budget: int, max_side=(2048, 2048), reg: float = 0.1, tol: float = 1e-4,
                  precision: str = "fp32", max_jobs: int = 8192, ctl_slots: int = 256,
-                 run_seconds: float = 600.0, max_rounds: int = 4):
+                 run_seconds: float = 600.0, max_rounds: int = 4, tuning: dict | None = None):
         import torch
         if precision not in ("fp32", "bf16x3"):
             raise ValueError("precision must be 'fp32' or 'bf16x3'")
@@ -130,6 +130,7 @@ class Server:
             raise ValueError("D must be (K, P, L0, L1)")
         self.D, self.reg, self.tol, self.max_rounds = D, float(reg), float(tol), int(max_rounds)
         self.precision = precision
+        self.tuning = tuning  # size class -> sub-domain side and stop margin (autotune.tune)
         self.device = D.device
         K, P, L0, L1 = D.shape
         self.stream = torch.cuda.Stream(device=self.device)  # copies, beta-init, refresh
@@ -187,7 +188,11 @@ class Server:
 
     def _submit(self, r: Request, warm: bool):
         _, beta, Z = r._dev
-        j = self.q.submit(beta, Z, r.lam, self.tol, warm_start=warm, stream=self.stream)
+        opts = None
+        if self.tuning:
+            from .autotune import opts_for
+            opts = opts_for(self.tuning, max(int(r.X.shape[1]), int(r.X.shape[2])))
+        j = self.q.submit(beta, Z, r.lam, self.tol, warm_start=warm, stream=self.stream, opts=opts)
         self.active[j] = r
         self.n_free_ctl -= 1
 

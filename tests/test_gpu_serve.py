@@ -118,3 +118,33 @@ def test_served_bf16x3_same_results(pkg, served):
     _check_done(mp)
     for a, b in zip(ref, mp):
         assert abs(a.objective - b.objective) <= REL * abs(a.objective)
+
+
+def test_autotuned_options_same_results(pkg, served):
+    """The autotuner picks a sub-domain side and stop margin per size class
+    (here the two smallest classes); serving with its table changes the
+    schedule, not the results."""
+    from paper_1901_09235_gb300 import autotune, serve
+    from synthetic import make_image_device
+    D, imgs = served
+    Dd = dev(D)
+
+    def make_image(side, seed):
+        w = Workload("tune", P, K, (side, side), L, SERVED_ATOMS["density"], SERVED_ATOMS["sigma"])
+        return make_image_device(w, 900 + seed, D)
+
+    table = autotune.tune(Dd, make_image, classes=[0, 1], reps=1)
+    assert set(table) == {"0", "1"}
+    for e in table.values():
+        assert e["sub"] in autotune.sub_candidates(L[0]) and 0 < e["stop_margin"] <= 1
+        assert e["ms"] == min(e["tried"].values())
+    small = [x for x in imgs if max(x.shape[1:]) <= 192]
+    arr = np.zeros(len(small))
+    with serve.Server(Dd, hbm_budget=1 << 30, max_side=(512, 512), run_seconds=120.0) as srv:
+        ref = srv.serve(_requests(serve, small, arr))
+    with serve.Server(Dd, hbm_budget=1 << 30, max_side=(512, 512), run_seconds=120.0, tuning=table) as srv:
+        tuned = srv.serve(_requests(serve, small, arr))
+    _check_done(ref)
+    _check_done(tuned)
+    for a, b in zip(ref, tuned):
+        assert abs(a.objective - b.objective) <= REL * abs(a.objective)

@@ -126,3 +126,26 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert len(lines) == 1
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_autotune_classes_and_candidates():
+    from paper_1901_09235_gb300 import autotune as at
+    assert [at.size_class(s) for s in (64, 96, 97, 384, 385, 1536, 1537, 2048)] == [0, 0, 1, 2, 3, 4, 5, 5]
+    sides = [at.class_side(c) for c in range(6)]
+    assert sides == sorted(sides) and sides[0] >= 64 and sides[-1] <= 2048
+    for c, sd in enumerate(sides):
+        assert at.size_class(sd) == c
+    assert at.sub_candidates(12) == [12, 16, 24, 32, 48]
+    assert 2 * 12 in at.sub_candidates(12)  # seeded at the paper's 2 L
+
+
+def test_autotune_table_to_opts(tmp_path):
+    from paper_1901_09235_gb300 import autotune as at
+    table = {"2": {"sub": 32, "stop_margin": 0.95, "ms": 1.0, "side": 271, "tried": {}}}
+    p = tmp_path / "t.json"
+    at.save(table, str(p))
+    assert at.load_table(str(p)) == table
+    o = at.opts_for(table, 300)
+    assert list(o.sub) == [32, 32] and abs(o.stop_margin - 0.95) < 1e-12
+    d = at.opts_for(table, 2000)  # class without an entry: defaults
+    assert list(d.sub) == [0, 0] and d.stop_margin == 0.0
