@@ -112,28 +112,43 @@ __global__ void __launch_bounds__(NT) nz_write_kernel(const float *Z, long long 
         }
 }
 
-// psi: a CTA takes a chunk of nonzeros; thread e owns entry (p, tau) of
-// every atom in shared memory, so no two threads touch the same word.
+// psi: a CTA takes a chunk of nonzeros (staged in shared memory as atom,
+// row, column, value); thread e owns entry (p, tau) of every atom in shared
+// memory, so no two threads touch the same word, and keeps eight X loads in
+// flight per pass over the chunk.
+constexpr int kPsiChunk = 64;
+
 template <int NT>
 __global__ void __launch_bounds__(NT) psi_kernel(const int *nk, const int *ns, const float *nzv,
                                                  const WsHeader *h, const float *X, double *psi64,
-                                                 int P, int K, int T0, int T1, int L0, int L1, int Z1,
-                                                 int chunk) {
+                                                 int P, int K, int T0, int T1, int L0, int L1, int Z1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *acc = reinterpret_cast<float *>(smem_raw);
+    __shared__ int c_k[kPsiChunk], c_off[kPsiChunk];
+    __shared__ float c_z[kPsiChunk];
     const int LL = L0 * L1, per = P * LL;
     const int cnt = h->scan_total;
-    const int lo = blockIdx.x * chunk, hi = min(cnt, lo + chunk);
-    if (lo >= hi) return;
+    const int lo = blockIdx.x * kPsiChunk, n = min(cnt, lo + kPsiChunk) - lo;
+    if (n <= 0) return;
     for (int q = threadIdx.x; q < K * per; q += NT) acc[q] = 0.f;
+    for (int q = threadIdx.x; q < n; q += NT) {
+        const int s = ns[lo + q], i = s / Z1;
+        c_k[q] = nk[lo + q];
+        c_off[q] = i * T1 + (s - i * Z1);  // X offset of the window's corner
+        c_z[q] = nzv[lo + q];
+    }
     __syncthreads();
-    for (int n = lo; n < hi; n++) {
-        const int k = nk[n], s = ns[n];
-        const float z = nzv[n];
-        const int i = s / Z1, j = s % Z1;
-        for (int e = threadIdx.x; e < per; e += NT) {
-            int p = e / LL, r = e % LL;
-            acc[k * per + e] += z * X[((size_t)p * T0 + i + r / L1) * T1 + j + r % L1];
+    for (int e = threadIdx.x; e < per; e += NT) {
+        const int p = e / LL, r = e - p * LL, d0 = r / L1, d1 = r - d0 * L1;
+        const float *xp = X + (size_t)p * T0 * T1 + (size_t)d0 * T1 + d1;
+        for (int n0 = 0; n0 < n; n0 += 8) {
+            float xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (n0 + u < n) xv[u] = __ldg(xp + c_off[n0 + u]);
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (n0 + u < n) acc[c_k[n0 + u] * per + e] += c_z[n0 + u] * xv[u];
         }
     }
     __syncthreads();
@@ -205,14 +220,14 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
     CSC_CUDA(cudaMemsetAsync(phi64, 0, (size_t)g.ntab() * sizeof(double), st));
     CSC_CUDA(cudaMemsetAsync(psi64, 0, (size_t)g.nd() * sizeof(double), st));
     if (total > 0) {
-        const int chunk = 64;
+        const int chunk = kPsiChunk;
         size_t smem = (size_t)g.nd() * sizeof(float);
         if (smem > 227 * 1024) return CSC_ERR_UNIMPLEMENTED;
         if (smem > 48 * 1024)
             CSC_CUDA(cudaFuncSetAttribute(psi_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         psi_kernel<256><<<(int)ceil_div(total, chunk), 256, smem, st>>>(
-            nk, ns, nzv, h, X, psi64, g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z1, chunk);
+            nk, ns, nzv, h, X, psi64, g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z1);
         phi_pairs_kernel<<<(int)ceil_div(total, 128), 128, 0, st>>>(nk, ns, nzv, h, phi64, g.K, g.L0,
                                                                     g.L1, g.Z0, g.Z1);
     }
