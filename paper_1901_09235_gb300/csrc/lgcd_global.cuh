@@ -78,6 +78,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
     __shared__ int s_ctl[2][2];                  // flag bumps seen, stop state
     __shared__ real s_lo[NW], s_hi[NW];          // soft-lock maxima per warp
     __shared__ int s_pause;
+    __shared__ volatile int s_block;  // a warp found a soft-lock blocker
     // state only thread 0 uses, kept out of every thread's registers
     __shared__ unsigned long long s_deadline;
     __shared__ real s_guard;
@@ -182,6 +183,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
             s_ctl[par][1] = state;
         }
         if (lane == 0) s_red[par][warp] = c;
+        if (threadIdx.x == 0) s_block = 0;  // read after the barrier below
         __syncthreads();
         if (s_ctl[par][1]) break;
         const int got = s_ctl[par][0];
@@ -201,6 +203,27 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         const bool active = best.a >= a.eps;
         bool accepted = false;
         int li0 = 0, lj0 = 0;
+        if (use_mask) {
+            // pull the next dirty sub-domain's beta and Z rows into L2 while
+            // this iteration's soft-lock and window update run (one line per
+            // row start; rows of a sub-domain span at most a few lines)
+            const unsigned long long rest = (active ? dmask : dmask & ~(1ull << m));
+            const unsigned long long above = m + 1 < 64 ? (rest >> (m + 1)) << (m + 1) : 0ull;
+            const int mn = above ? __ffsll((long long)above) - 1 : (rest ? __ffsll((long long)rest) - 1 : -1);
+            if (mn >= 0 && mn != m) {
+                const int nr = mn / ns1, nc = mn - nr * ns1;
+                const int pr0 = nr * a.sub0, pc0 = nc * a.sub1;
+                const int pbh = min(a.sub0, h - pr0), pbw = min(a.sub1, wd - pc0);
+                const int lines = (pbw + 31) >> 5;  // 128-byte lines per row, at most
+                for (int q = threadIdx.x; q < K * pbh * lines; q += NT) {
+                    const int k = q / (pbh * lines), rem = q - k * (pbh * lines), rr = rem / lines;
+                    const int cc = (rem - rr * lines) * 32;
+                    const size_t g = (size_t)k * plane + (size_t)(or0 + pr0 + rr) * a.Z1 + oc0 + pc0 + cc;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.beta + g));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Z + g));
+                }
+            }
+        }
         if (active) {
             const unsigned pos = best.key / (unsigned)K;
             const int k0 = (int)(best.key - pos * (unsigned)K);
@@ -225,6 +248,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                 const int unA = ((nA + kRowBlock - 1) / kRowBlock) * nchA;
                 const int per_k = unA + ((nB + kRowBlock - 1) / kRowBlock) * nchB;
                 for (int u = warp; u < K * per_k; u += NW) {
+                    if (s_block) break;  // another warp already rejects best
                     const int k = u / per_k, rem = u - k * per_k;
                     const bool inA = rem < unA;
                     const int nchS = inA ? nchA : nchB, remS = inA ? rem : rem - unA;
@@ -257,6 +281,9 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                             else hi = max(hi, d);
                         }
                     }
+                    // a blocker: best loses to a lower-ranked tile on a tie,
+                    // to a higher-ranked one only when strictly smaller
+                    if (__any_sync(0xffffffffu, lo >= best.a || hi > best.a) && lane == 0) s_block = 1;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
