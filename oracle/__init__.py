@@ -62,6 +62,7 @@ def _load():
             "orc_beta_from_Z_at": (None, [i, i, i, i, i, i, p, p, p, ll, p, p, p]),
             "orc_objective_sparse": (d, [i, i, i, i, i, i, p, p, p, d]),
             "orc_objective_nz": (d, [i, i, i, i, i, i, p, p, C.c_longlong, p, p, p, p, d]),
+            "orc_rcd": (ll, [i, i, i, i, i, i, p, d, p, ll, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -197,6 +198,24 @@ def lgcd(X, D, lam: float, eps: float, sub=None, tile=None, max_updates: int = 0
         n = min(cap, out["n_updates"])
         out["trace"] = dict(k0=tk[:n], s0=ts[:n], z_old=tzo[:n], z_new=tzn[:n], beta=tb[:n])
     return out
+
+
+def rcd(X, D, lam: float, coords, Z=None, beta=None):
+    """Coordinate descent over the flat indices ``coords`` (k |Omega| + s), in
+    order (the RCD baseline of Section 5.1 when the order is random).  Starts
+    from ``Z`` / ``beta`` (default: Z = 0, beta = D~ * X) and returns
+    (Z, beta, number of coordinates that changed)."""
+    X, D = _f64(X), _f64(D)
+    g = _geom(X, D)
+    if Z is None:
+        Z = np.zeros(_zshape(X, D))
+        beta = beta_init(X, D)
+    Z, beta = _f64(Z).copy(), _f64(beta).copy()
+    cs = np.ascontiguousarray(coords, dtype=np.uint32)
+    n = _load().orc_rcd(*g, _ptr(D), float(lam), _ptr(cs), len(cs), _ptr(Z), _ptr(beta))
+    if n < 0:
+        raise ValueError("coordinate index outside K x Omega")
+    return Z, beta, int(n)
 
 
 def phi_psi(Z, X, L):

@@ -366,6 +366,49 @@ int orc_lgcd(int P, int K, int T0, int T1, int L0, int L1,
                           tr_k0, tr_s0, tr_zold, tr_znew, tr_beta);
 }
 
+/* Coordinate descent in a given order: the randomized baseline (RCD) of the
+ * selection comparison (Section 5.1, Fig. compare_cd) when the order is drawn
+ * uniformly at random.  For each flat index c = k |Omega| + s of coords[0..n)
+ * in turn, Z_k[s] <- Z'_k[s] = ST(beta_k[s], lambda) / ||D_k||^2 (Eq.
+ * pb_coord), followed by the beta update of Eq. beta_update when the value
+ * changes.  The order is an input so that the caller chooses its
+ * distribution.  beta and Z are the state on entry and on exit (Z = 0 with
+ * beta = D~ * X is the cold start of Alg. 1).  Returns the number of
+ * coordinates whose value changed, or -1 for an index outside K x Omega. */
+long long orc_rcd(int P, int K, int T0, int T1, int L0, int L1, const double *D, double lambda,
+                  const unsigned *coords, long long n, double *Z, double *beta)
+{
+    int Z0 = T0 - L0 + 1, Z1 = T1 - L1 + 1;
+    int W0 = 2 * L0 - 1, W1 = 2 * L1 - 1;
+    size_t plane = (size_t)Z0 * Z1;
+    double *C = malloc((size_t)K * K * W0 * W1 * sizeof(double));
+    double *nrm = malloc((size_t)K * sizeof(double));
+    orc_dtd(P, K, L0, L1, D, C);
+    orc_atom_sqnorms(P, K, L0, L1, D, nrm);
+    long long changed = 0;
+    for (long long q = 0; q < n; q++) {
+        size_t c = coords[q];
+        if (c >= (size_t)K * plane) { changed = -1; break; }
+        int k0 = (int)(c / plane), s = (int)(c % plane), i0 = s / Z1, j0 = s % Z1;
+        double znew = soft_threshold(beta[c], lambda) / nrm[k0];
+        double dz = znew - Z[c];
+        if (dz == 0.0) continue;
+        Z[c] = znew;
+        changed++;
+        for (int k = 0; k < K; k++)
+            for (int d0 = -L0 + 1; d0 < L0; d0++)
+                for (int d1 = -L1 + 1; d1 < L1; d1++) {
+                    int i = i0 + d0, j = j0 + d1;
+                    if (i < 0 || i >= Z0 || j < 0 || j >= Z1) continue;
+                    if (k == k0 && d0 == 0 && d1 == 0) continue;
+                    beta[IDX3(k, i, j, Z0, Z1)] -= C[IDX4(k, k0, d0 + L0 - 1, d1 + L1 - 1, K, W0, W1)] * dz;
+                }
+    }
+    free(C);
+    free(nrm);
+    return changed;
+}
+
 /* ---------------------------------------------------------------------------
  * Dictionary update (Section 4.2).
  * ------------------------------------------------------------------------ */

@@ -445,3 +445,72 @@ def test_cdl_loop_one_tap_closed_form(orc, dims, d0):
     assert abs(float(D.reshape(-1)[0]) - d) <= 1e-9
     np.testing.assert_allclose(Z.reshape(-1), z, rtol=0, atol=1e-9)
     np.testing.assert_allclose(np.asarray(trace), np.asarray(costs), rtol=1e-10, atol=0)
+
+
+# ---------------------------------------------------------------- RCD
+def _rcd_problem():
+    from synthetic import Workload, make_problem
+    w = Workload("rcd_pin", P=2, K=3, T=(120,), L=(8,), density=0.03, sigma=0.1)
+    X, D, _ = make_problem(w, 17)
+    return X, D
+
+
+def test_rcd_step_is_the_coordinate_minimiser(orc):
+    """One step of orc.rcd lands at the minimum of the objective along that
+    coordinate, found by a dense grid search of the objective itself."""
+    X, D = _rcd_problem()
+    lam = 0.1 * orc.lambda_max(X, D)
+    rng = np.random.default_rng(3)
+    Z = np.zeros((3, 113))
+    Z[rng.integers(0, 3, 6), rng.integers(0, 113, 6)] = rng.standard_normal(6)
+    beta = orc.beta_from_Z(X, D, Z)
+    for c in (5, 120, 300):
+        k, s = divmod(c, 113)
+        Z1, _, _ = orc.rcd(X, D, lam, [c], Z=Z, beta=beta)
+        z_star = Z1[k, s]
+        grid = z_star + np.linspace(-0.05, 0.05, 201)
+        vals = []
+        for zg in grid:
+            Zg = Z.copy()
+            Zg[k, s] = zg
+            vals.append(orc.objective(X, D, Zg, lam))
+        assert abs(grid[int(np.argmin(vals))] - z_star) <= 0.0005 + 1e-12
+        assert orc.objective(X, D, Z1, lam) <= min(vals) + 1e-12
+
+
+def test_rcd_objective_never_increases_and_beta_stays_consistent(orc):
+    X, D = _rcd_problem()
+    lam = 0.1 * orc.lambda_max(X, D)
+    coords = np.random.default_rng(5).integers(0, 3 * 113, 2000).astype(np.uint32)
+    Z, beta = None, None
+    prev = np.inf
+    for chunk in np.array_split(coords, 20):
+        Z, beta, _ = orc.rcd(X, D, lam, chunk, Z=Z, beta=beta)
+        f = orc.objective(X, D, Z, lam)
+        assert f <= prev * (1 + 1e-12)
+        prev = f
+    assert np.abs(beta - orc.beta_from_Z(X, D, Z)).max() < 1e-9
+
+
+def test_rcd_cyclic_order_reaches_the_greedy_solution(orc):
+    """The LASSO minimiser is unique: cyclic CD (RCD with the sequential
+    order) and greedy CD (LGCD with one sub-domain) reach the same objective,
+    and both pass the KKT test."""
+    X, D = _rcd_problem()
+    lam = 0.1 * orc.lambda_max(X, D)
+    order = np.arange(3 * 113, dtype=np.uint32)
+    Z, beta = None, None
+    for _ in range(400):
+        Z, beta, changed = orc.rcd(X, D, lam, order, Z=Z, beta=beta)
+        if orc.kkt(X, D, Z, lam) < 1e-10:
+            break
+    g = orc.lgcd(X, D, lam, 1e-10, sub=(113,))
+    f_c, f_g = orc.objective(X, D, Z, lam), orc.objective(X, D, g["Z"], lam)
+    assert abs(f_c - f_g) <= 1e-9 * abs(f_g)
+    assert orc.kkt(X, D, Z, lam) < 1e-8 and orc.kkt(X, D, g["Z"], lam) < 1e-8
+
+
+def test_rcd_rejects_indices_outside_the_domain(orc):
+    X, D = _rcd_problem()
+    with pytest.raises(ValueError):
+        orc.rcd(X, D, 0.1, [3 * 113])
