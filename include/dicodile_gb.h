@@ -234,6 +234,23 @@ CSC_API int csc_refresh_beta(const csc_shape *shape, const float *X, const float
                              float lambda, float *beta, double *max_dz_out, double *objective_out,
                              void *workspace, size_t workspace_bytes, csc_stream_t stream);
 
+/* Coordinate descent in a given order on one worker: the randomized
+ * baseline (RCD) of the coordinate-selection comparison (Section 5.1) when
+ * the order is drawn at random.  For each flat index c = k |Omega| + s of
+ * coords[0..n) (device, uint32) in turn, Z_k[s] <- ST(beta_k[s], lambda) /
+ * ||D_k||^2 (Eq. pb_coord) with the beta update of Eq. beta_update when the
+ * value changes -- the same result as one coordinate at a time.  beta, Z:
+ * in/out, a consistent state (Z = 0 with beta from csc_init_beta for a cold
+ * start); dtd from csc_init_beta.  updates_out (host, may be NULL): the
+ * number of coordinates that changed.  Synchronises the stream.
+ * CSC_ERR_INVALID for an index outside K x Omega (the walk stops there);
+ * CSC_ERR_TIMEOUT after 60 s.  Greedy CD and cyclic CD need no separate
+ * call: csc_lgcd_solve with one worker and one sub-domain covering the domain
+ * (greedy) or sub-domains of one position (cyclic) (Section 3). */
+CSC_API int csc_rcd_solve(const csc_shape *shape, const float *D, const float *dtd, float *beta, float *Z,
+                          float lambda, const unsigned *coords, long long n, long long *updates_out,
+                          void *workspace, size_t workspace_bytes, csc_stream_t stream);
+
 /* Batched solves: many images of uneven size in one persistent launch.
  * A persistent grid (two CTAs of 256 threads per SM) takes the tiles of queued
  * images (jobs) in order and runs the global-memory LGCD worker (Alg. 3) on

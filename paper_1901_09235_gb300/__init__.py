@@ -100,6 +100,7 @@ def load():
         "cdl_dict_update": (i, [S, p, p, d, p, i, d, C.POINTER(d), C.POINTER(i), p, sz, p]),
         "cdl_fit": (i, [S, p, p, p, p, p, p, p, d, d, i, d, i, d, O, p, sz, C.POINTER(d), C.POINTER(i), p]),
         "csc_refresh_beta": (i, [S, p, p, p, C.c_float, p, C.POINTER(d), C.POINTER(d), p, sz, p]),
+        "csc_rcd_solve": (i, [S, p, p, p, p, C.c_float, p, C.c_longlong, C.POINTER(C.c_longlong), p, sz, p]),
         "csc_queue_workspace_size": (i, [S, i, i, C.POINTER(sz), C.POINTER(sz)]),
         "csc_queue_create": (i, [S, p, p, O, i, i, p, sz, p, sz, d, p, p, C.POINTER(p)]),
         "csc_queue_submit": (i, [p, i, i, p, p, C.c_float, C.c_float, i, O, C.POINTER(i)]),
@@ -303,6 +304,28 @@ def csc_refresh_beta(X, D, Z, lam: float, beta=None, ws=None, stream=None):
                                    C.byref(mdz), C.byref(obj), _ptr(ws), ws.numel(), _stream(stream)),
            "csc_refresh_beta")
     return beta, mdz.value, obj.value
+
+
+def csc_rcd_solve(X_shape, D, dtd, beta, Z, lam: float, coords, ws=None, stream=None) -> int:
+    """Coordinate descent over the flat indices ``coords`` (a uint32-valued
+    CUDA tensor, k |Omega| + s), in order (csc_rcd_solve).  beta and Z are
+    updated in place.  Returns the number of coordinates that changed."""
+    import torch
+    for t, n in ((D, "D"), (dtd, "dtd"), (beta, "beta"), (Z, "Z")):
+        _need(t, torch.float32, n)
+    if not isinstance(coords, torch.Tensor) or not coords.is_cuda or coords.dtype not in (torch.int32,
+                                                                                        torch.uint32):
+        raise TypeError("coords must be a CUDA int32 / uint32 tensor")
+    if not coords.is_contiguous():
+        raise ValueError("coords must be contiguous")
+    s = make_shape(tuple(X_shape), tuple(D.shape))
+    if ws is None:
+        ws = workspace(s, device=D.device)
+    upd = C.c_longlong(0)
+    _check(load().csc_rcd_solve(C.byref(s), _ptr(D), _ptr(dtd), _ptr(beta), _ptr(Z), float(lam), _ptr(coords),
+                                coords.numel(), C.byref(upd), _ptr(ws), ws.numel(), _stream(stream)),
+           "csc_rcd_solve")
+    return upd.value
 
 
 class Queue:
