@@ -31,6 +31,7 @@ class Workload:
     nonneg: bool = False
     reg: float = 0.1          # lambda = reg * lambda_max
     tol: float = 1e-4         # stop when max |dZ| < tol
+    amp: float = 1.0          # standard deviation of the nonzero activations
 
 
 # The workloads named in the project's benchmark configuration.
@@ -41,6 +42,10 @@ IMAGE_4096 = Workload("csc2d_4096x4096_P1_K25_L32", 1, 25, (4096, 4096), (32, 32
 IMAGE_8192 = Workload("csc2d_8192x8192_P1_K25_L32", 1, 25, (8192, 8192), (32, 32), 5e-5, 0.05,
                       nonneg=True)
 SERVED_ATOMS = dict(P=3, K=16, L=(12, 12), density=0.002, sigma=0.1)
+# coordinate-selection comparison on one worker (Section 5.1): 7 channels, 25
+# atoms of 250, rho = 0.007, activations N(0, 10^2), noise variance 1
+SELECTION_150L = Workload("selection_T150L_P7_K25_L250", 7, 25, (150 * 250,), (250,), 0.007, 1.0, amp=10.0)
+SELECTION_750L = Workload("selection_T750L_P7_K25_L250", 7, 25, (750 * 250,), (250,), 0.007, 1.0, amp=10.0)
 
 
 def scaled(w: Workload, T: tuple, name: str | None = None) -> Workload:
@@ -84,11 +89,11 @@ def make_problem(w: Workload, seed: int, D: np.ndarray | None = None):
         for k in range(w.K):
             cnt = int(rng.binomial(n, w.density))
             pos = rng.choice(n, size=cnt, replace=False)
-            amp = rng.standard_normal(cnt)
+            amp = w.amp * rng.standard_normal(cnt)
             Z[k].reshape(-1)[pos] = np.abs(amp) if w.nonneg else amp
     else:
         mask = rng.random((w.K,) + Tz) < w.density
-        amp = rng.standard_normal((w.K,) + Tz)
+        amp = w.amp * rng.standard_normal((w.K,) + Tz)
         if w.nonneg:
             amp = np.abs(amp)
         Z[...] = np.where(mask, amp, 0.0)
@@ -129,7 +134,7 @@ def make_image_device(w: Workload, seed: int, D: np.ndarray, device="cuda"):
     for k in range(w.K):
         cnt = int(rng.binomial(n, w.density))
         pos = rng.choice(n, size=cnt, replace=False)
-        amp = rng.standard_normal(cnt)
+        amp = w.amp * rng.standard_normal(cnt)
         if w.nonneg:
             amp = np.abs(amp)
         Zd[k, torch.from_numpy(pos).to(device)] = torch.from_numpy(amp.astype(np.float32)).to(device)
