@@ -228,6 +228,27 @@ def max_over_ranks(values, device=None):
     return [float(x) for x in t.cpu()]
 
 
+def l2_copy_gbs(device, mib=32, iters=50):
+    """L2 bandwidth probe: a device copy of a buffer that fits L2 twice over
+    (read + write bytes per second, CUDA events, best of three runs).  The
+    measured-peaks file holds HBM and tensor peaks only."""
+    import torch
+    a = torch.ones(mib * (1 << 20) // 4, dtype=torch.float32, device=device)
+    b = torch.empty_like(a)
+    best = 0.0
+    for _ in range(3):
+        for _ in range(5):
+            b.copy_(a)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(iters):
+            b.copy_(a)
+        e.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * a.numel() * 4 * iters / (s.elapsed_time(e) / 1e3) / 1e9)
+    return best
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -258,26 +279,26 @@ def cpu_oracle_step(X, D0, w):
     lam = w.reg * lm
     out = oracle.lgcd(X, D0, lam, w.tol)
     Z = out["Z"]
-    oracle.objective(X, D0, Z, lam)
+    obj = oracle.objective(X, D0, Z, lam)
     phi, psi = oracle.phi_psi(Z, X, w.L)
     xs = float((X.astype(np.float64) ** 2).sum())
     oracle.pgd_armijo(phi, psi, xs, D0, max_iter=50, tol=1e-8)
-    return time.perf_counter() - t0, out["n_updates"]
+    return time.perf_counter() - t0, out["n_updates"], obj
 
 
 def cpu_baseline(X, D0, w, seconds):
     import oracle
     oracle.build()
-    done, total, upd = 0, 0.0, 0
+    done, total, upd, obj = 0, 0.0, 0, None
     while total < seconds and done < 20:
-        dt, u = cpu_oracle_step(X, D0, w)
+        dt, u, obj = cpu_oracle_step(X, D0, w)
         total += dt
         upd += u
         done += 1
     return {"value": done / total, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} full oracle steps of the same workload (lambda_max, LGCD, objective, "
                       f"phi/psi, PGD) on one core, {total:.1f} s",
-            "updates_per_s": upd / total}
+            "updates_per_s": upd / total, "objective": obj}
 
 
 # ------------------------------------------------------------ served trace
@@ -509,6 +530,10 @@ def image_main(args):
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                          "algorithmic_bytes_per_launch": abytes / len(stats), "Z_entries": nz},
             "e2e": None, "gpu_launches": None, "clocks": clocks}
+    l2 = l2_copy_gbs(device)
+    line["roofline_l2"] = {"bound": "l2", "kernel": "lgcd_global_kernel", "achieved": achieved, "peak": l2,
+                           "unit": "GB/s", "frac": achieved / l2,
+                           "peak_source": "measured in this run: 32 MiB device copy, read + write bytes"}
     print(json.dumps(line))
     return 0
 
@@ -700,7 +725,7 @@ def main():
         times = []
         upd = 0
         for _ in range(args.steps):
-            dt, u = cpu_oracle_step(X, D0, w)
+            dt, u, _ = cpu_oracle_step(X, D0, w)
             times.append(dt)
             upd += u
         total = sum(times)
@@ -805,7 +830,12 @@ def main():
         "clocks": clocks,
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(X, D0, w, args.cpu_seconds)
+        cb = cpu_baseline(X, D0, w, args.cpu_seconds)
+        obj_ref = cb.pop("objective")
+        line["cpu_baseline"] = cb
+        # the same solve's objective against the FP64 oracle's (both at tol)
+        line["objective_oracle"] = obj_ref
+        line["objective_rel_err_vs_oracle"] = abs(last["objective"] - obj_ref) / abs(obj_ref)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
