@@ -117,6 +117,121 @@ __global__ void __launch_bounds__(NT) corr_kernel(CorrArgs<real> a) {
     block_max_atomic<NT>(m, a.bits);
 }
 
+// 1-D rows (T0 = L0 = 1), FP32: thread t owns the NQ consecutive positions
+// t NQ .. t NQ + NQ - 1 of the CTA's segment and KC atoms.  Taps go in blocks
+// of NQ: the 2 NQ signal values x[t NQ + tb ..] held in registers serve the
+// NQ x NQ products of every atom, so each shared-memory word feeds NQ KC
+// FMAs.  Weights are staged tap-major (the KC atoms of a tap contiguous, a
+// broadcast), taps padded with zero weights to a multiple of NQ.  Every
+// output accumulates channel by channel and tap by tap, as corr_kernel does.
+template <int NT, int NQ, int KC, int EPI>
+__global__ void __launch_bounds__(NT) corr1d_kernel(CorrArgs<float> a) {
+    constexpr int TC = NT * NQ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = a.L1, Lp = (L + NQ - 1) / NQ * NQ;
+    float *sS = reinterpret_cast<float *>(smem_raw);  // TC + Lp + NQ signal values
+    float *sW = sS + TC + Lp + NQ;                     // Lp x KC weights
+    const int j0 = blockIdx.x * TC, k0 = blockIdx.y * KC, s0 = threadIdx.x * NQ;
+    float acc[KC][NQ];
+#pragma unroll
+    for (int kk = 0; kk < KC; kk++)
+#pragma unroll
+        for (int q = 0; q < NQ; q++) acc[kk][q] = 0.f;
+    for (int p = 0; p < a.P; p++) {
+        __syncthreads();
+        const float *Sp = a.S + (size_t)p * a.T1;
+        for (int e = threadIdx.x; e < TC + Lp + NQ; e += NT) {
+            const int gj = j0 + e;
+            sS[e] = gj < a.T1 ? Sp[gj] : 0.f;
+        }
+        for (int e = threadIdx.x; e < Lp * KC; e += NT) {
+            const int t = e / KC, kk = e - t * KC, k = k0 + kk;
+            sW[e] = (t < L && k < a.K) ? a.Wt[((size_t)k * a.P + p) * L + t] : 0.f;
+        }
+        __syncthreads();
+        for (int tb = 0; tb < Lp; tb += NQ) {
+            float x[2 * NQ];
+#pragma unroll
+            for (int i = 0; i < 2 * NQ; i += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(sS + s0 + tb + i);
+                x[i] = v.x;
+                x[i + 1] = v.y;
+                x[i + 2] = v.z;
+                x[i + 3] = v.w;
+            }
+#pragma unroll
+            for (int u = 0; u < NQ; u++) {
+                const float *wt = sW + (tb + u) * KC;
+#pragma unroll
+                for (int kk = 0; kk < KC; kk++) {
+                    const float wv = wt[kk];
+#pragma unroll
+                    for (int q = 0; q < NQ; q++) acc[kk][q] = fmaf(wv, x[q + u], acc[kk][q]);
+                }
+            }
+        }
+    }
+    unsigned long long m = 0;
+#pragma unroll
+    for (int kk = 0; kk < KC; kk++) {
+        const int k = k0 + kk;
+        if (k >= a.K) continue;
+        float nr = 0.f, inv = 0.f;
+        if (EPI == EPI_REFRESH) {
+            const double nk = a.nrm[k];
+            nr = (float)nk;
+            inv = (float)(1.0 / nk);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const int j = j0 + s0 + q;
+            if (j >= a.Z1) continue;
+            const size_t at = (size_t)k * a.Z1 + j;
+            float v = acc[kk][q];
+            if (EPI == EPI_INIT) {
+                a.out[at] = v;
+                const unsigned long long b = nonneg_bits(v < 0.f ? -v : v);
+                m = b > m ? b : m;
+            } else {
+                const float z = a.Zc[at];
+                v = v + nr * z;
+                a.out[at] = v;
+                float dz = coord_update(v, a.lambda, nr, inv) - z;
+                dz = dz < 0.f ? -dz : dz;
+                const unsigned long long b = nonneg_bits(dz);
+                m = b > m ? b : m;
+            }
+        }
+    }
+    block_max_atomic<NT>(m, a.bits);
+}
+
+template <int NT, int NQ, int KC, int EPI>
+static int run_corr1d(const Geom &g, CorrArgs<float> a, cudaStream_t st) {
+    constexpr int TC = NT * NQ;
+    auto kern = corr1d_kernel<NT, NQ, KC, EPI>;
+    const int Lp = (g.L1 + NQ - 1) / NQ * NQ;
+    const size_t smem = ((size_t)TC + Lp + NQ + (size_t)Lp * KC) * sizeof(float);
+    if (smem > 48 * 1024) {
+        if (smem > 227 * 1024) return CSC_ERR_UNIMPLEMENTED;
+        CSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    dim3 grid((unsigned)ceil_div(g.Z1, TC), (unsigned)ceil_div(g.K, KC));
+    kern<<<grid, NT, smem, st>>>(a);
+    CSC_CUDA(cudaGetLastError());
+    return CSC_OK;
+}
+
+template <int EPI>
+static int corr1d_dispatch(const Geom &g, CorrArgs<float> a, cudaStream_t st) {
+    // 128 threads x 4 positions: measured fastest on the 1-D workload (P = 5,
+    // T = 200,000, K = 10, L = 64) among 64 / 128 / 256 threads x 4 / 8
+    if (g.K <= 4) return run_corr1d<128, 4, 4, EPI>(g, a, st);
+    if (g.K <= 8) return run_corr1d<128, 4, 8, EPI>(g, a, st);
+    if (g.K <= 10) return run_corr1d<128, 4, 10, EPI>(g, a, st);
+    return run_corr1d<128, 4, 16, EPI>(g, a, st);
+}
+
 template <typename real, int NT, int TR, int NQ, int KC, int EPI>
 static int run_corr(const Geom &g, CorrArgs<real> a, cudaStream_t st) {
     constexpr int TC = (NT / TR) * NQ;
@@ -134,6 +249,9 @@ static int run_corr(const Geom &g, CorrArgs<real> a, cudaStream_t st) {
 
 template <typename real, int EPI>
 static int corr_dispatch(const Geom &g, CorrArgs<real> a, cudaStream_t st) {
+    if constexpr (sizeof(real) == 4) {
+        if (g.Z0 == 1 && g.L0 == 1) return corr1d_dispatch<EPI>(g, a, st);
+    }
     if (g.Z0 == 1) return run_corr<real, 256, 1, 4, 8, EPI>(g, a, st);
     return run_corr<real, 256, 8, 4, 8, EPI>(g, a, st);
 }
@@ -252,6 +370,14 @@ int preload_corr_kernels() {
         (const void *)corr_kernel<float, 256, 1, 4, 8, EPI_INIT>,
         (const void *)corr_kernel<float, 256, 8, 4, 8, EPI_REFRESH>,
         (const void *)corr_kernel<float, 256, 1, 4, 8, EPI_REFRESH>,
+        (const void *)corr1d_kernel<128, 4, 4, EPI_INIT>,
+        (const void *)corr1d_kernel<128, 4, 8, EPI_INIT>,
+        (const void *)corr1d_kernel<128, 4, 10, EPI_INIT>,
+        (const void *)corr1d_kernel<128, 4, 16, EPI_INIT>,
+        (const void *)corr1d_kernel<128, 4, 4, EPI_REFRESH>,
+        (const void *)corr1d_kernel<128, 4, 8, EPI_REFRESH>,
+        (const void *)corr1d_kernel<128, 4, 10, EPI_REFRESH>,
+        (const void *)corr1d_kernel<128, 4, 16, EPI_REFRESH>,
         (const void *)dtd_kernel<float, 256>,
         (const void *)atom_norm_kernel<float, 256>,
     };
