@@ -23,7 +23,11 @@
  *    dtd[k][k2][delta + L - 1] = sum_p sum_tau D_kp[tau] D_k2p[tau + delta].
  *  - All array pointers are DEVICE pointers owned by the caller; the library
  *    never allocates device memory.  Scratch space is a caller-owned device
- *    buffer of at least csc_workspace_size() bytes.
+ *    buffer of at least csc_workspace_size() bytes.  Host scalars read back
+ *    from the device (and the queue's control records) pass through one 8 KB
+ *    pinned host buffer per calling host thread, allocated on first use and
+ *    kept until the process ends: copies through pageable memory cost
+ *    hundreds of microseconds on the GB300 platform.
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
  *    stream).  Calls that return a host scalar or a stats struct synchronise
  *    that stream before returning; this is stated per call.

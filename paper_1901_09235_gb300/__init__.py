@@ -50,11 +50,12 @@ class SolveStats(C.Structure):
                 ("t_exit_us", C.c_double), ("wakeups", C.c_longlong),
                 ("phase_cycles", C.c_longlong * 6), ("status", C.c_int)]
 
+    _arrays = ("tiles", "tile_size", "phase_cycles")
+
     def as_dict(self):
-        out = {}
-        for name, _ in self._fields_:
-            v = getattr(self, name)
-            out[name] = list(v) if hasattr(v, "__len__") else v
+        out = {name: getattr(self, name) for name, _ in self._fields_}
+        for name in self._arrays:
+            out[name] = list(out[name])
         return out
 
 
@@ -270,8 +271,9 @@ def csc_lgcd_solve(X, D, dtd, beta, lam: float, tol: float, Z=None, opts: SolveO
     fn = load().csc_lgcd_solve_f64 if f64 else load().csc_lgcd_solve
     rc = fn(C.byref(s), _ptr(X), _ptr(D), _ptr(dtd), _ptr(beta), _ptr(Z), lam, tol, C.byref(opts),
             _ptr(ws), ws.numel(), C.byref(st), _stream(stream))
-    _check(rc, "csc_lgcd_solve", soft=(CSC_NOT_CONVERGED, CSC_ERR_DIVERGED), stats=st.as_dict())
-    return Z, st.as_dict()
+    stats = st.as_dict()
+    _check(rc, "csc_lgcd_solve", soft=(CSC_NOT_CONVERGED, CSC_ERR_DIVERGED), stats=stats)
+    return Z, stats
 
 
 def csc_objective(X, D, Z, lam: float, ws=None, stream=None) -> float:

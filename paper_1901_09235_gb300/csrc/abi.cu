@@ -14,6 +14,19 @@ int set_cuda_error(cudaError_t e) {
     return CSC_ERR_CUDA;
 }
 
+void *pinned_scratch() {
+    static thread_local void *buf = nullptr;
+    static thread_local bool failed = false;
+    if (!buf && !failed) {
+        if (cudaHostAlloc(&buf, kPinnedScratch, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            buf = nullptr;
+            failed = true;
+        }
+    }
+    return buf;
+}
+
 int make_geom(const csc_shape *s, Geom *g) {
     if (!s || !g) return CSC_ERR_INVALID;
     if (s->d != 1 && s->d != 2) return CSC_ERR_INVALID;
@@ -111,8 +124,7 @@ static int init_beta_impl(const csc_shape *shape, const real *X, const real *D, 
     if (rc) return rc;
     if (lmax) {
         unsigned long long bits = 0;
-        CSC_CUDA(cudaMemcpyAsync(&bits, &h->lmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, st));
-        CSC_CUDA(cudaStreamSynchronize(st));
+        if ((rc = read_back(&bits, &h->lmax_bits, st))) return rc;
         if (sizeof(real) == 4) {
             unsigned u = (unsigned)bits;
             float f;
@@ -192,8 +204,10 @@ int csc_objective(const csc_shape *shape, const float *X, const float *D, const 
     rc = launch_refresh<float>(g, L, wsb, X, D, Z, 0.f, nullptr, st);
     if (rc) return rc;
     WsHeader hh;
-    CSC_CUDA(cudaMemcpyAsync(&hh, wsb + L.hdr, sizeof(hh), cudaMemcpyDeviceToHost, st));
-    CSC_CUDA(cudaStreamSynchronize(st));
+    {
+        const int rb_ = read_back(&hh, wsb + L.hdr, st);
+        if (rb_) return rb_;
+    }
     *objective_out = 0.5 * hh.obj_f + lambda * hh.obj_g;
     return CSC_OK;
 }

@@ -46,8 +46,10 @@ extern "C" int cdl_fit(const csc_shape *shape, const float *X, float *D, float *
     sumsq_kernel<256><<<1216, 256, 0, st>>>(X, g.nx(), &h->obj_f);
     CSC_CUDA(cudaGetLastError());
     double xsq = 0.0;
-    CSC_CUDA(cudaMemcpyAsync(&xsq, &h->obj_f, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CSC_CUDA(cudaStreamSynchronize(st));
+    {
+        const int rb_ = read_back(&xsq, &h->obj_f, st);
+        if (rb_) return rb_;
+    }
 
     csc_solve_opts o;
     csc_default_opts(&o);

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/dicodile_gb.h"
 
@@ -223,6 +224,30 @@ int launch_corr_refresh(const Geom &g, const real *R, const real *D, const real 
                         unsigned long long *maxdz_bits, cudaStream_t st);
 template <typename real>
 int launch_dtd(const Geom &g, const real *D, real *dtd, cudaStream_t st);
+
+// Small host <-> device transfers (scalars read back, control records) go
+// through one pinned host buffer per host thread, allocated on first use and
+// kept for the thread's lifetime (never freed: freeing pinned memory can wait
+// for the whole device).  A copy to or from pageable memory costs hundreds of
+// microseconds on this platform, a pinned one a few.
+constexpr size_t kPinnedScratch = 8192;
+void *pinned_scratch();  // kPinnedScratch bytes, or nullptr when it cannot be allocated
+
+// dst <- *src_dev (device), then the stream is synchronised
+template <typename T>
+int read_back(T *dst, const void *src_dev, cudaStream_t st) {
+    static_assert(sizeof(T) <= kPinnedScratch, "small transfers only");
+    void *s = pinned_scratch();
+    if (s) {
+        CSC_CUDA(cudaMemcpyAsync(s, src_dev, sizeof(T), cudaMemcpyDeviceToHost, st));
+        CSC_CUDA(cudaStreamSynchronize(st));
+        memcpy(dst, s, sizeof(T));
+    } else {
+        CSC_CUDA(cudaMemcpyAsync(dst, src_dev, sizeof(T), cudaMemcpyDeviceToHost, st));
+        CSC_CUDA(cudaStreamSynchronize(st));
+    }
+    return CSC_OK;
+}
 
 // Load the FP32 kernels of beta-init / refresh / objective (and the tensor-core
 // beta-init) into the context now.  With lazy module loading a kernel is

@@ -478,9 +478,8 @@ extern "C" int csc_init_beta_bf16x3(const csc_shape *shape, const float *X, cons
     if (lambda_max_out) {
         unsigned bits = 0;
         int err = 0;
-        CSC_CUDA(cudaMemcpyAsync(&bits, &h->lmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, st));
-        CSC_CUDA(cudaMemcpyAsync(&err, &h->overflow, sizeof(err), cudaMemcpyDeviceToHost, st));
-        CSC_CUDA(cudaStreamSynchronize(st));
+        if ((rc = read_back(&bits, &h->lmax_bits, st))) return rc;
+        if ((rc = read_back(&err, &h->overflow, st))) return rc;
         if (err) return CSC_ERR_TIMEOUT;
         float f;
         memcpy(&f, &bits, 4);

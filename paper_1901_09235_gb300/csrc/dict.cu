@@ -213,8 +213,10 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
     nz_count_kernel<256><<<nblk, 256, 0, st>>>(Z, zpos, g.K, blk_cnt);
     nz_scan_kernel<1024><<<1, 1024, 0, st>>>(blk_cnt, blk_off, nblk, h);
     int total = 0;
-    CSC_CUDA(cudaMemcpyAsync(&total, &h->scan_total, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CSC_CUDA(cudaStreamSynchronize(st));
+    {
+        const int rb_ = read_back(&total, &h->scan_total, st);
+        if (rb_) return rb_;
+    }
     if (total > L.nnz_cap) return CSC_ERR_WORKSPACE;
     nz_write_kernel<256><<<nblk, 256, 0, st>>>(Z, zpos, g.K, blk_off, h, L.nnz_cap, nk, ns, nzv);
     CSC_CUDA(cudaMemsetAsync(phi64, 0, (size_t)g.ntab() * sizeof(double), st));
@@ -739,8 +741,10 @@ int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x
     CSC_CUDA(cudaLaunchKernelEx(&cfg, pgd_kernel, a));
     if (obj_out || it_out) {
         double out[3];
-        CSC_CUDA(cudaMemcpyAsync(out, h->pgd_out, sizeof(out), cudaMemcpyDeviceToHost, st));
-        CSC_CUDA(cudaStreamSynchronize(st));
+        {
+            const int rb_ = read_back(out, h->pgd_out, st);
+            if (rb_) return rb_;
+        }
         if (obj_out) *obj_out = out[0];
         if (it_out) *it_out = (int)out[1];
     }

@@ -505,8 +505,10 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
         rc = launch_refresh<real>(g, L, wsb, X, D, Z, lambda, beta, st);
         if (rc) return rc;
         S.refresh_rounds++;
-        CSC_CUDA(cudaMemcpyAsync(&hh, hdr, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
-        CSC_CUDA(cudaStreamSynchronize(st));
+        {
+            const int rb_ = read_back(&hh, hdr, st);
+            if (rb_) return rb_;
+        }
         float ms = 0.f;
         CSC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         kms_total += ms;

@@ -272,9 +272,11 @@ int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, c
                                              (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return set_cuda_error(e);
     }
-    // the kernels that run beside the persistent one are loaded before it starts
+    // the kernels that run beside the persistent one are loaded, and this
+    // thread's pinned scratch allocated, before it starts
     if ((rc = preload_corr_kernels()) || (rc = preload_residual_kernels()) || (rc = preload_umma_kernels()))
         return rc;
+    pinned_scratch();
     csc_queue *q = new csc_queue();
     q->atoms = g;
     q->D = D;
@@ -388,15 +390,28 @@ int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float 
     memset(&h0, 0, sizeof(h0));
     h0.pending = W;
     cudaStream_t ss = q->sstream;
+    const int j = q->njobs, nj = j + 1;
+    // the three records are copied from the pinned scratch (regions that do
+    // not overlap), falling back to this stack frame; the copies are waited
+    // for before returning either way
+    static_assert(sizeof(WsHeader) + sizeof(QueueJob) + 2 * 256 <= kPinnedScratch, "scratch layout");
+    unsigned char *ps = static_cast<unsigned char *>(pinned_scratch());
+    const void *src_h = &h0, *src_j = &job, *src_n = &nj;
+    if (ps) {
+        const size_t oj = q_align(sizeof(WsHeader)), on = oj + q_align(sizeof(QueueJob));
+        memcpy(ps, &h0, sizeof(h0));
+        memcpy(ps + oj, &job, sizeof(job));
+        memcpy(ps + on, &nj, sizeof(int));
+        src_h = ps;
+        src_j = ps + oj;
+        src_n = ps + on;
+    }
     if (!warm_start) CSC_CUDA(cudaMemsetAsync(Z, 0, (size_t)g.nz() * sizeof(float), ss));
-    CSC_CUDA(cudaMemcpyAsync(hdr, &h0, sizeof(h0), cudaMemcpyHostToDevice, ss));
+    CSC_CUDA(cudaMemcpyAsync(hdr, src_h, sizeof(h0), cudaMemcpyHostToDevice, ss));
     CSC_CUDA(cudaMemsetAsync(flags, 0, (size_t)W * kDirs * 32 * sizeof(int), ss));
-    const int j = q->njobs;
     q->host[j].complete = 0;
-    CSC_CUDA(cudaMemcpyAsync(q->jobs + j, &job, sizeof(job), cudaMemcpyHostToDevice, ss));
-    const int nj = j + 1;
-    CSC_CUDA(cudaMemcpyAsync(&q->qc->njobs, &nj, sizeof(int), cudaMemcpyHostToDevice, ss));
-    // the source values above live on this stack frame: wait for the copies
+    CSC_CUDA(cudaMemcpyAsync(q->jobs + j, src_j, sizeof(job), cudaMemcpyHostToDevice, ss));
+    CSC_CUDA(cudaMemcpyAsync(&q->qc->njobs, src_n, sizeof(int), cudaMemcpyHostToDevice, ss));
     CSC_CUDA(cudaStreamSynchronize(ss));
     q->njobs = nj;
     q->next_slot += W;
@@ -432,9 +447,9 @@ int csc_queue_inspect(csc_queue *q, int job, long long *out) {
     if (!q || !out || job < 0 || job >= q->njobs) return CSC_ERR_INVALID;
     QueueCtl c;
     QueueJob jb;
-    CSC_CUDA(cudaMemcpyAsync(&c, q->qc, sizeof(c), cudaMemcpyDeviceToHost, q->sstream));
-    CSC_CUDA(cudaMemcpyAsync(&jb, q->jobs + job, sizeof(jb), cudaMemcpyDeviceToHost, q->sstream));
-    CSC_CUDA(cudaStreamSynchronize(q->sstream));
+    int rc;
+    if ((rc = read_back(&c, q->qc, q->sstream))) return rc;
+    if ((rc = read_back(&jb, q->jobs + job, q->sstream))) return rc;
     out[0] = jb.prefix;
     out[1] = jb.W;
     out[2] = jb.claimed;
@@ -448,9 +463,10 @@ int csc_queue_inspect(csc_queue *q, int job, long long *out) {
 
 int csc_queue_close(csc_queue *q) {
     if (!q) return CSC_ERR_INVALID;
-    const int one = 1;
     int rc = CSC_OK;
-    cudaError_t e = cudaMemcpyAsync(&q->qc->close, &one, sizeof(int), cudaMemcpyHostToDevice, q->sstream);
+    // the close word is 0 since creation: setting its low byte makes it 1
+    // (a device-side write, no host source)
+    cudaError_t e = cudaMemsetAsync(&q->qc->close, 1, 1, q->sstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->sstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->kstream);
     if (e != cudaSuccess) rc = set_cuda_error(e);
@@ -475,8 +491,10 @@ int csc_refresh_beta(const csc_shape *shape, const float *X, const float *D, con
     rc = launch_refresh<float>(g, L, wsb, X, D, Z, lambda, beta, st);
     if (rc) return rc;
     WsHeader hh;
-    CSC_CUDA(cudaMemcpyAsync(&hh, wsb + L.hdr, sizeof(hh), cudaMemcpyDeviceToHost, st));
-    CSC_CUDA(cudaStreamSynchronize(st));
+    {
+        const int rb_ = read_back(&hh, wsb + L.hdr, st);
+        if (rb_) return rb_;
+    }
     if (max_dz_out) {
         const unsigned u = (unsigned)hh.maxdz_bits;
         float f;

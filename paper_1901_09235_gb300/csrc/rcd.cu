@@ -150,8 +150,10 @@ extern "C" int csc_rcd_solve(const csc_shape *shape, const float *D, const float
     rcd_kernel<<<1, kRcdThreads, 2 * (size_t)g.K * sizeof(float), st>>>(a);
     CSC_CUDA(cudaGetLastError());
     WsHeader hh;
-    CSC_CUDA(cudaMemcpyAsync(&hh, hdr, sizeof(hh), cudaMemcpyDeviceToHost, st));
-    CSC_CUDA(cudaStreamSynchronize(st));
+    {
+        const int rb_ = read_back(&hh, hdr, st);
+        if (rb_) return rb_;
+    }
     if (updates_out) *updates_out = (long long)hh.stat[ST_UPDATES];
     return hh.stop;
 }
