@@ -742,7 +742,7 @@ int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x
     if (obj_out || it_out) {
         double out[3];
         {
-            const int rb_ = read_back(out, h->pgd_out, st);
+            const int rb_ = read_back(&out, h->pgd_out, st);  // all three values
             if (rb_) return rb_;
         }
         if (obj_out) *obj_out = out[0];

@@ -154,3 +154,22 @@ def test_queue_limits(pkg):
         with pytest.raises(pkg.CscError) as e:
             q.submit(extra[2][0], extra[2][1], r.lam, TOL)
         assert e.value.status == pkg.CSC_ERR_WORKSPACE
+
+
+def test_queue_degenerate_and_thin_images(pkg):
+    """A 1 x 1 activation map (image = atom size), thin strips in both
+    orientations and a small square, mixed in one queue: each matches the
+    plain single solve."""
+    D = _atoms(19)
+    Dd = dev(D)
+    shapes = [(12, 12), (13, 300), (400, 14), (30, 30), (12, 700)]
+    reqs = [_Req(pkg, _image(s0, s1, 80 + i, D), Dd) for i, (s0, s1) in enumerate(shapes)]
+    with pkg.Queue(Dd, reqs[0].dtd, max_jobs=64, ctl_slots=16, run_seconds=60.0) as q:
+        jobs = [q.submit(r.beta, r.Z, r.lam, TOL) for r in reqs]
+        objs = [_finish(pkg, q, r, Dd, j)[0] for r, j in zip(reqs, jobs)]
+    for r, obj in zip(reqs, objs):
+        beta, _, _ = pkg.csc_init_beta(r.X, Dd)
+        Z, st = pkg.csc_lgcd_solve(r.X, Dd, r.dtd, beta, r.lam, TOL)
+        assert st["status"] == 0
+        ref = pkg.csc_objective(r.X, Dd, Z, float(np.float32(r.lam)))
+        assert abs(obj - ref) <= REL * abs(ref) + 1e-9, (tuple(r.X.shape), obj, ref)

@@ -148,3 +148,24 @@ def test_autotuned_options_same_results(pkg, served):
     _check_done(tuned)
     for a, b in zip(ref, tuned):
         assert abs(a.objective - b.objective) <= REL * abs(a.objective)
+
+
+def test_served_result_copied_out_and_budget_enforced(pkg, served):
+    """Z_out receives the solution whose objective the server reports; a
+    request that cannot fit the HBM budget is refused before serving."""
+    import torch
+    from paper_1901_09235_gb300 import serve
+    D, imgs = served
+    Dd = dev(D)
+    x = imgs[0]
+    zs = (K, x.shape[1] - L[0] + 1, x.shape[2] - L[1] + 1)
+    z_out = torch.empty(zs, dtype=torch.float32, pin_memory=True)
+    with serve.Server(Dd, hbm_budget=1 << 28, max_side=(512, 512), run_seconds=60.0) as srv:
+        (r,) = srv.serve([serve.Request(X=x, Z_out=z_out)])
+    assert r.status == 0
+    obj = pkg.csc_objective(dev(x.numpy()), Dd, z_out.cuda(), float(np.float32(r.lam)))
+    assert abs(obj - r.objective) <= 1e-12 * abs(obj) + 1e-12
+    small = serve.footprint(tuple(D.shape), tuple(x.shape))
+    with serve.Server(Dd, hbm_budget=small - 256, max_side=(512, 512), run_seconds=60.0) as srv:
+        with pytest.raises(ValueError):
+            srv.serve([serve.Request(X=x)])
