@@ -117,21 +117,24 @@ __global__ void __launch_bounds__(NT) corr_kernel(CorrArgs<real> a) {
     block_max_atomic<NT>(m, a.bits);
 }
 
-// 1-D rows (T0 = L0 = 1), FP32: thread t owns the NQ consecutive positions
-// t NQ .. t NQ + NQ - 1 of the CTA's segment and KC atoms.  Taps go in blocks
-// of NQ: the 2 NQ signal values x[t NQ + tb ..] held in registers serve the
-// NQ x NQ products of every atom, so each shared-memory word feeds NQ KC
-// FMAs.  Weights are staged tap-major (the KC atoms of a tap contiguous, a
-// broadcast), taps padded with zero weights to a multiple of NQ.  Every
-// output accumulates channel by channel and tap by tap, as corr_kernel does.
-template <int NT, int NQ, int KC, int EPI>
-__global__ void __launch_bounds__(NT) corr1d_kernel(CorrArgs<float> a) {
-    constexpr int TC = NT * NQ;
+// FP32 correlations by rows: a CTA covers TR output rows x TC columns for KC
+// atoms; thread (r, c) owns the NQ consecutive positions (i0 + r, j0 + c NQ
+// + q).  Taps go in blocks of NQ along a tap row: the 2 NQ signal values of
+// row i0 + r + tau0 held in registers serve the NQ x NQ products of every
+// atom, so each shared-memory word feeds NQ KC FMAs.  Weights are staged
+// tap-major (the KC atoms of a tap contiguous, a broadcast), tap columns
+// padded with zero weights to a multiple of NQ.  Every output accumulates
+// channel by channel, tap row by tap row and tap by tap, as corr_kernel does.
+template <int NT, int TR, int NQ, int KC, int EPI>
+__global__ void __launch_bounds__(NT) corr_rows_kernel(CorrArgs<float> a) {
+    constexpr int TPR = NT / TR, TC = TPR * NQ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int L = a.L1, Lp = (L + NQ - 1) / NQ * NQ;
-    float *sS = reinterpret_cast<float *>(smem_raw);  // TC + Lp + NQ signal values
-    float *sW = sS + TC + Lp + NQ;                     // Lp x KC weights
-    const int j0 = blockIdx.x * TC, k0 = blockIdx.y * KC, s0 = threadIdx.x * NQ;
+    const int L0 = a.L0, L1 = a.L1, Lp = (L1 + NQ - 1) / NQ * NQ;
+    const int PR = TR + L0 - 1, PC = (TC + Lp + NQ + 3) / 4 * 4;  // patch rows, padded row length
+    float *sS = reinterpret_cast<float *>(smem_raw);  // PR x PC signal patch
+    float *sW = sS + (size_t)PR * PC;                  // L0 x Lp x KC weights
+    const int i0 = blockIdx.y * TR, j0 = blockIdx.x * TC, k0 = blockIdx.z * KC;
+    const int r = threadIdx.x / TPR, s0 = (threadIdx.x % TPR) * NQ;
     float acc[KC][NQ];
 #pragma unroll
     for (int kk = 0; kk < KC; kk++)
@@ -139,43 +142,48 @@ __global__ void __launch_bounds__(NT) corr1d_kernel(CorrArgs<float> a) {
         for (int q = 0; q < NQ; q++) acc[kk][q] = 0.f;
     for (int p = 0; p < a.P; p++) {
         __syncthreads();
-        const float *Sp = a.S + (size_t)p * a.T1;
-        for (int e = threadIdx.x; e < TC + Lp + NQ; e += NT) {
-            const int gj = j0 + e;
-            sS[e] = gj < a.T1 ? Sp[gj] : 0.f;
+        const float *Sp = a.S + (size_t)p * a.T0 * a.T1;
+        for (int e = threadIdx.x; e < PR * PC; e += NT) {
+            const int rr = e / PC, cc = e - rr * PC, gi = i0 + rr, gj = j0 + cc;
+            sS[e] = (gi < a.T0 && gj < a.T1) ? Sp[(size_t)gi * a.T1 + gj] : 0.f;
         }
-        for (int e = threadIdx.x; e < Lp * KC; e += NT) {
-            const int t = e / KC, kk = e - t * KC, k = k0 + kk;
-            sW[e] = (t < L && k < a.K) ? a.Wt[((size_t)k * a.P + p) * L + t] : 0.f;
+        for (int e = threadIdx.x; e < L0 * Lp * KC; e += NT) {
+            const int tt = e / KC, kk = e - tt * KC, ta = tt / Lp, tb = tt - ta * Lp, k = k0 + kk;
+            sW[e] = (tb < L1 && k < a.K) ? a.Wt[(((size_t)k * a.P + p) * L0 + ta) * L1 + tb] : 0.f;
         }
         __syncthreads();
-        for (int tb = 0; tb < Lp; tb += NQ) {
-            float x[2 * NQ];
+        for (int ta = 0; ta < L0; ta++) {
+            const float *row = sS + (size_t)(r + ta) * PC + s0;
+            const float *wta = sW + (size_t)ta * Lp * KC;
+            for (int tb = 0; tb < Lp; tb += NQ) {
+                float x[2 * NQ];
 #pragma unroll
-            for (int i = 0; i < 2 * NQ; i += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(sS + s0 + tb + i);
-                x[i] = v.x;
-                x[i + 1] = v.y;
-                x[i + 2] = v.z;
-                x[i + 3] = v.w;
-            }
+                for (int i = 0; i < 2 * NQ; i += 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(row + tb + i);
+                    x[i] = v.x;
+                    x[i + 1] = v.y;
+                    x[i + 2] = v.z;
+                    x[i + 3] = v.w;
+                }
 #pragma unroll
-            for (int u = 0; u < NQ; u++) {
-                const float *wt = sW + (tb + u) * KC;
+                for (int u = 0; u < NQ; u++) {
+                    const float *wt = wta + (tb + u) * KC;
 #pragma unroll
-                for (int kk = 0; kk < KC; kk++) {
-                    const float wv = wt[kk];
+                    for (int kk = 0; kk < KC; kk++) {
+                        const float wv = wt[kk];
 #pragma unroll
-                    for (int q = 0; q < NQ; q++) acc[kk][q] = fmaf(wv, x[q + u], acc[kk][q]);
+                        for (int q = 0; q < NQ; q++) acc[kk][q] = fmaf(wv, x[q + u], acc[kk][q]);
+                    }
                 }
             }
         }
     }
     unsigned long long m = 0;
+    const int i = i0 + r;
 #pragma unroll
     for (int kk = 0; kk < KC; kk++) {
         const int k = k0 + kk;
-        if (k >= a.K) continue;
+        if (k >= a.K || i >= a.Z0) continue;
         float nr = 0.f, inv = 0.f;
         if (EPI == EPI_REFRESH) {
             const double nk = a.nrm[k];
@@ -186,7 +194,7 @@ __global__ void __launch_bounds__(NT) corr1d_kernel(CorrArgs<float> a) {
         for (int q = 0; q < NQ; q++) {
             const int j = j0 + s0 + q;
             if (j >= a.Z1) continue;
-            const size_t at = (size_t)k * a.Z1 + j;
+            const size_t at = ((size_t)k * a.Z0 + i) * a.Z1 + j;
             float v = acc[kk][q];
             if (EPI == EPI_INIT) {
                 a.out[at] = v;
@@ -206,30 +214,35 @@ __global__ void __launch_bounds__(NT) corr1d_kernel(CorrArgs<float> a) {
     block_max_atomic<NT>(m, a.bits);
 }
 
-template <int NT, int NQ, int KC, int EPI>
-static int run_corr1d(const Geom &g, CorrArgs<float> a, cudaStream_t st) {
-    constexpr int TC = NT * NQ;
-    auto kern = corr1d_kernel<NT, NQ, KC, EPI>;
+template <int NT, int TR, int NQ, int KC, int EPI>
+static int run_corr_rows(const Geom &g, CorrArgs<float> a, cudaStream_t st) {
+    constexpr int TC = (NT / TR) * NQ;
+    auto kern = corr_rows_kernel<NT, TR, NQ, KC, EPI>;
     const int Lp = (g.L1 + NQ - 1) / NQ * NQ;
-    const size_t smem = ((size_t)TC + Lp + NQ + (size_t)Lp * KC) * sizeof(float);
-    if (smem > 48 * 1024) {
-        if (smem > 227 * 1024) return CSC_ERR_UNIMPLEMENTED;
+    const int PR = TR + g.L0 - 1, PC = (TC + Lp + NQ + 3) / 4 * 4;
+    const size_t smem = ((size_t)PR * PC + (size_t)g.L0 * Lp * KC) * sizeof(float);
+    if (smem > 227 * 1024) return CSC_ERR_UNIMPLEMENTED;
+    if (smem > 48 * 1024)
         CSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
-    dim3 grid((unsigned)ceil_div(g.Z1, TC), (unsigned)ceil_div(g.K, KC));
+    dim3 grid((unsigned)ceil_div(g.Z1, TC), (unsigned)ceil_div(g.Z0, TR), (unsigned)ceil_div(g.K, KC));
     kern<<<grid, NT, smem, st>>>(a);
     CSC_CUDA(cudaGetLastError());
     return CSC_OK;
 }
 
 template <int EPI>
-static int corr1d_dispatch(const Geom &g, CorrArgs<float> a, cudaStream_t st) {
-    // 128 threads x 4 positions: measured fastest on the 1-D workload (P = 5,
-    // T = 200,000, K = 10, L = 64) among 64 / 128 / 256 threads x 4 / 8
-    if (g.K <= 4) return run_corr1d<128, 4, 4, EPI>(g, a, st);
-    if (g.K <= 8) return run_corr1d<128, 4, 8, EPI>(g, a, st);
-    if (g.K <= 10) return run_corr1d<128, 4, 10, EPI>(g, a, st);
-    return run_corr1d<128, 4, 16, EPI>(g, a, st);
+static int corr_rows_dispatch(const Geom &g, CorrArgs<float> a, cudaStream_t st) {
+    if (g.Z0 == 1) {
+        // 1-D: 128 threads x 4 positions, measured fastest on the 1-D workload
+        // (P = 5, T = 200,000, K = 10, L = 64) among 64 / 128 / 256 x 4 / 8
+        if (g.K <= 4) return run_corr_rows<128, 1, 4, 4, EPI>(g, a, st);
+        if (g.K <= 8) return run_corr_rows<128, 1, 4, 8, EPI>(g, a, st);
+        if (g.K <= 10) return run_corr_rows<128, 1, 4, 10, EPI>(g, a, st);
+        return run_corr_rows<128, 1, 4, 16, EPI>(g, a, st);
+    }
+    // 2-D: 4 rows x 128 columns per CTA
+    if (g.K <= 8) return run_corr_rows<128, 4, 4, 8, EPI>(g, a, st);
+    return run_corr_rows<128, 4, 4, 16, EPI>(g, a, st);
 }
 
 template <typename real, int NT, int TR, int NQ, int KC, int EPI>
@@ -250,7 +263,8 @@ static int run_corr(const Geom &g, CorrArgs<real> a, cudaStream_t st) {
 template <typename real, int EPI>
 static int corr_dispatch(const Geom &g, CorrArgs<real> a, cudaStream_t st) {
     if constexpr (sizeof(real) == 4) {
-        if (g.Z0 == 1 && g.L0 == 1) return corr1d_dispatch<EPI>(g, a, st);
+        const int rc = corr_rows_dispatch<EPI>(g, a, st);
+        if (rc != CSC_ERR_UNIMPLEMENTED) return rc;  // too large for shared memory: the generic kernel
     }
     if (g.Z0 == 1) return run_corr<real, 256, 1, 4, 8, EPI>(g, a, st);
     return run_corr<real, 256, 8, 4, 8, EPI>(g, a, st);
@@ -370,14 +384,18 @@ int preload_corr_kernels() {
         (const void *)corr_kernel<float, 256, 1, 4, 8, EPI_INIT>,
         (const void *)corr_kernel<float, 256, 8, 4, 8, EPI_REFRESH>,
         (const void *)corr_kernel<float, 256, 1, 4, 8, EPI_REFRESH>,
-        (const void *)corr1d_kernel<128, 4, 4, EPI_INIT>,
-        (const void *)corr1d_kernel<128, 4, 8, EPI_INIT>,
-        (const void *)corr1d_kernel<128, 4, 10, EPI_INIT>,
-        (const void *)corr1d_kernel<128, 4, 16, EPI_INIT>,
-        (const void *)corr1d_kernel<128, 4, 4, EPI_REFRESH>,
-        (const void *)corr1d_kernel<128, 4, 8, EPI_REFRESH>,
-        (const void *)corr1d_kernel<128, 4, 10, EPI_REFRESH>,
-        (const void *)corr1d_kernel<128, 4, 16, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<128, 1, 4, 4, EPI_INIT>,
+        (const void *)corr_rows_kernel<128, 1, 4, 8, EPI_INIT>,
+        (const void *)corr_rows_kernel<128, 1, 4, 10, EPI_INIT>,
+        (const void *)corr_rows_kernel<128, 1, 4, 16, EPI_INIT>,
+        (const void *)corr_rows_kernel<128, 4, 4, 8, EPI_INIT>,
+        (const void *)corr_rows_kernel<128, 4, 4, 16, EPI_INIT>,
+        (const void *)corr_rows_kernel<128, 1, 4, 4, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<128, 1, 4, 8, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<128, 1, 4, 10, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<128, 1, 4, 16, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<128, 4, 4, 8, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<128, 4, 4, 16, EPI_REFRESH>,
         (const void *)dtd_kernel<float, 256>,
         (const void *)atom_norm_kernel<float, 256>,
     };
