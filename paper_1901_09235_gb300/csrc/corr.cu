@@ -240,8 +240,11 @@ static int corr_rows_dispatch(const Geom &g, CorrArgs<float> a, cudaStream_t st)
         if (g.K <= 10) return run_corr_rows<128, 1, 4, 10, EPI>(g, a, st);
         return run_corr_rows<128, 1, 4, 16, EPI>(g, a, st);
     }
-    // 2-D: 4 rows x 128 columns per CTA
+    // 2-D: 4 rows x 128 columns per CTA; the atom chunk (8, 13 or 16) that
+    // pads K least (25 atoms: two chunks of 13)
     if (g.K <= 8) return run_corr_rows<128, 4, 4, 8, EPI>(g, a, st);
+    const long long w13 = ceil_div(g.K, 13) * 13, w16 = ceil_div(g.K, 16) * 16;
+    if (w13 < w16) return run_corr_rows<128, 4, 4, 13, EPI>(g, a, st);
     return run_corr_rows<128, 4, 4, 16, EPI>(g, a, st);
 }
 
@@ -389,12 +392,14 @@ int preload_corr_kernels() {
         (const void *)corr_rows_kernel<128, 1, 4, 10, EPI_INIT>,
         (const void *)corr_rows_kernel<128, 1, 4, 16, EPI_INIT>,
         (const void *)corr_rows_kernel<128, 4, 4, 8, EPI_INIT>,
+        (const void *)corr_rows_kernel<128, 4, 4, 13, EPI_INIT>,
         (const void *)corr_rows_kernel<128, 4, 4, 16, EPI_INIT>,
         (const void *)corr_rows_kernel<128, 1, 4, 4, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 1, 4, 8, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 1, 4, 10, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 1, 4, 16, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 4, 4, 8, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<128, 4, 4, 13, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 4, 4, 16, EPI_REFRESH>,
         (const void *)dtd_kernel<float, 256>,
         (const void *)atom_norm_kernel<float, 256>,
