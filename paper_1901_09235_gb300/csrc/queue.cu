@@ -344,8 +344,7 @@ int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float 
     if (rc) return rc;
     const int W = pl.G0 * pl.G1;
     if (W > q->grid) return CSC_ERR_UNIMPLEMENTED;
-    const int cs = q->free_ctl.back();
-    q->free_ctl.pop_back();
+    const int cs = q->free_ctl.back();  // taken below once the job is published
     unsigned char *ctl = q->ctl_pool + (size_t)cs * q->ctl_stride;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ctl);
     int *flags = reinterpret_cast<int *>(ctl + sizeof(WsHeader));
@@ -413,6 +412,7 @@ int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float 
     CSC_CUDA(cudaMemcpyAsync(q->jobs + j, src_j, sizeof(job), cudaMemcpyHostToDevice, ss));
     CSC_CUDA(cudaMemcpyAsync(&q->qc->njobs, src_n, sizeof(int), cudaMemcpyHostToDevice, ss));
     CSC_CUDA(cudaStreamSynchronize(ss));
+    q->free_ctl.pop_back();
     q->njobs = nj;
     q->next_slot += W;
     q->job_ctl.push_back(cs);

@@ -178,13 +178,22 @@ class Server:
         Z = self.arena.view(offs[2], zs, torch.float32)
         r._dev = (X, beta, Z)
         r.t_admit = now
-        with torch.cuda.stream(self.stream):
-            X.copy_(r.X, non_blocking=True)
-            init = csc_init_beta_bf16x3 if self.precision == "bf16x3" else csc_init_beta
-            _, _, lmax = init(X, self.D, beta=beta, dtd=self.dtd_scratch, ws=self.ws, stream=self.stream)
-        r.lam = self.reg * lmax
-        self._submit(r, warm=False)
+        try:
+            with torch.cuda.stream(self.stream):
+                X.copy_(r.X, non_blocking=True)
+                init = csc_init_beta_bf16x3 if self.precision == "bf16x3" else csc_init_beta
+                _, _, lmax = init(X, self.D, beta=beta, dtd=self.dtd_scratch, ws=self.ws, stream=self.stream)
+            r.lam = self.reg * lmax
+            self._submit(r, warm=False)
+        except Exception:
+            self._release(r)
+            raise
         return True
+
+    def _release(self, r: Request):
+        for o, n in r._alloc:
+            self.arena.release(o, n)
+        r._alloc, r._dev = [], None
 
     def _submit(self, r: Request, warm: bool):
         _, beta, Z = r._dev
@@ -216,9 +225,7 @@ class Server:
             with torch.cuda.stream(self.stream):
                 r.Z_out.copy_(Z, non_blocking=True)
             self.stream.synchronize()
-        for o, n in r._alloc:
-            self.arena.release(o, n)
-        r._alloc, r._dev = [], None
+        self._release(r)
         r.t_done = now_fn()
         return True
 
