@@ -390,7 +390,7 @@ def served_main(args):
             wt = Workload("tune", 3, 16, (side, side), (12, 12), SERVED_ATOMS["density"], SERVED_ATOMS["sigma"])
             return make_image_device(wt, 7_000_000 + seed, D, device)
 
-        tuning = autotune.tune(Dd, make_image)
+        tuning = autotune.tune(Dd, make_image, ctas_per_sm=3 if args.precision == "fp32" else 2)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         tune_s = time.perf_counter() - t0
@@ -431,7 +431,8 @@ def served_main(args):
         "warmup": len(warm), "ms_per_step": 1e3 * makespan / len(reqs), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (device-built images copied to pinned host memory)",
-        "config": dict(base_cfg, arm=f"served: persistent queue, {args.precision} beta-init"
+        "config": dict(base_cfg, arm=f"served: persistent queue ({3 if args.precision == 'fp32' else 2} CTAs "
+                       f"per SM), {args.precision} beta-init"
                        + (", autotuned sub-domains" if tuning else ", default sub-domains"),
                        pixels=n_px, timing="host wall clock from the first arrival to the last "
                        "result; every request's X copied in from pinned host memory"),

@@ -256,7 +256,7 @@ CSC_API int csc_rcd_solve(const csc_shape *shape, const float *D, const float *d
                           void *workspace, size_t workspace_bytes, csc_stream_t stream);
 
 /* Batched solves: many images of uneven size in one persistent launch.
- * A persistent grid (two CTAs of 256 threads per SM) takes the tiles of queued
+ * A persistent grid (two or three CTAs of 256 threads per SM) takes the tiles of queued
  * images (jobs) in order and runs the global-memory LGCD worker (Alg. 3) on
  * each; an image starts when all of its tiles are held.  Images share the atom
  * shape, the resident dictionary D and its D^T D table.  Jobs are appended
@@ -265,8 +265,9 @@ CSC_API int csc_rcd_solve(const csc_shape *shape, const float *D, const float *d
 typedef struct csc_queue csc_queue;
 
 /* Device and pinned-host workspace for a queue (atoms: d = 2, P, K, L; T is
- * ignored) holding up to max_jobs jobs in total, ctl_slots of them at once. */
-CSC_API int csc_queue_workspace_size(const csc_shape *atoms, int max_jobs, int ctl_slots,
+ * ignored) holding up to max_jobs jobs in total, ctl_slots of them at once,
+ * with the given grid density (as for csc_queue_create). */
+CSC_API int csc_queue_workspace_size(const csc_shape *atoms, int max_jobs, int ctl_slots, int ctas_per_sm,
                                      size_t *device_bytes, size_t *host_bytes);
 
 /* Start the persistent kernel on kernel_stream.  D [K][P][L0][L1] and dtd
@@ -281,9 +282,14 @@ CSC_API int csc_queue_workspace_size(const csc_shape *atoms, int max_jobs, int c
  * starts, so that they run beside it on every SM.  Other kernels that first
  * load while the queue runs may wait for it to end (lazy module loading). 
  * opts: tile / sub-domain sizes, mode, timeout of each solve (may be NULL).
+ * ctas_per_sm: 2 (0 = default) leaves each SM room for the tensor-core
+ * beta-init (csc_init_beta_bf16x3) beside the queue; 3 runs more tiles at
+ * once but leaves room only for the FP32 calls (csc_init_beta,
+ * csc_refresh_beta, csc_objective) -- a bf16x3 beta-init launched beside it
+ * would wait for the queue to end.  Other values: CSC_ERR_INVALID.
  * The library allocates only the host-side handle. */
 CSC_API int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd,
-                             const csc_solve_opts *opts, int max_jobs, int ctl_slots,
+                             const csc_solve_opts *opts, int max_jobs, int ctl_slots, int ctas_per_sm,
                              void *device_workspace, size_t device_bytes, void *host_workspace,
                              size_t host_bytes, double run_seconds, csc_stream_t kernel_stream,
                              csc_stream_t side_stream, csc_queue **queue_out);

@@ -102,8 +102,8 @@ def load():
         "cdl_fit": (i, [S, p, p, p, p, p, p, p, d, d, i, d, i, d, O, p, sz, C.POINTER(d), C.POINTER(i), p]),
         "csc_refresh_beta": (i, [S, p, p, p, C.c_float, p, C.POINTER(d), C.POINTER(d), p, sz, p]),
         "csc_rcd_solve": (i, [S, p, p, p, p, C.c_float, p, C.c_longlong, C.POINTER(C.c_longlong), p, sz, p]),
-        "csc_queue_workspace_size": (i, [S, i, i, C.POINTER(sz), C.POINTER(sz)]),
-        "csc_queue_create": (i, [S, p, p, O, i, i, p, sz, p, sz, d, p, p, C.POINTER(p)]),
+        "csc_queue_workspace_size": (i, [S, i, i, i, C.POINTER(sz), C.POINTER(sz)]),
+        "csc_queue_create": (i, [S, p, p, O, i, i, i, p, sz, p, sz, d, p, p, C.POINTER(p)]),
         "csc_queue_submit": (i, [p, i, i, p, p, C.c_float, C.c_float, i, O, C.POINTER(i)]),
         "csc_queue_poll": (i, [p, i, ST]),
         "csc_queue_close": (i, [p]),
@@ -339,10 +339,12 @@ class Queue:
     control copies on a second one; both are non-blocking streams.  While the
     queue is open nothing may wait for the whole device (torch.cuda.synchronize,
     the legacy default stream of a blocking stream): the kernel ends only on
-    close() or after run_seconds."""
+    close() or after run_seconds.  ctas_per_sm: 2 (0, the default) leaves room
+    beside the queue for the tensor-core beta-init; 3 runs more tiles at once
+    and leaves room for the FP32 calls only."""
 
     def __init__(self, D, dtd, max_jobs: int = 1024, ctl_slots: int = 256, run_seconds: float = 120.0,
-                 opts: SolveOpts | None = None):
+                 opts: SolveOpts | None = None, ctas_per_sm: int = 0):
         import torch
         _need(D, torch.float32, "D")
         _need(dtd, torch.float32, "dtd")
@@ -355,8 +357,8 @@ class Queue:
         self.atoms, self.D, self.dtd = s, D, dtd
         lib = load()
         db, hb = C.c_size_t(0), C.c_size_t(0)
-        _check(lib.csc_queue_workspace_size(C.byref(s), int(max_jobs), int(ctl_slots), C.byref(db),
-                                            C.byref(hb)), "csc_queue_workspace_size")
+        _check(lib.csc_queue_workspace_size(C.byref(s), int(max_jobs), int(ctl_slots), int(ctas_per_sm),
+                                            C.byref(db), C.byref(hb)), "csc_queue_workspace_size")
         self.ws = torch.empty(db.value, dtype=torch.uint8, device=D.device)
         self.host = torch.zeros(hb.value, dtype=torch.uint8, pin_memory=True)
         self.kernel_stream = torch.cuda.Stream(device=D.device)
@@ -367,7 +369,8 @@ class Queue:
         self._jobs = {}
         h = C.c_void_p(0)
         _check(lib.csc_queue_create(C.byref(s), _ptr(D), _ptr(dtd), C.byref(opts) if opts else None,
-                                    int(max_jobs), int(ctl_slots), _ptr(self.ws), self.ws.numel(),
+                                    int(max_jobs), int(ctl_slots), int(ctas_per_sm), _ptr(self.ws),
+                                    self.ws.numel(),
                                     C.c_void_p(self.host.data_ptr()), self.host.numel(), float(run_seconds),
                                     C.c_void_p(self.kernel_stream.cuda_stream),
                                     C.c_void_p(self.side_stream.cuda_stream), C.byref(h)), "csc_queue_create")

@@ -65,9 +65,9 @@ def load_table(path: str) -> dict:
 
 
 def tune(D, make_image, classes=None, margins=(0.99, 0.95, 0.9), reps: int = 2, reg: float = 0.1,
-         tol: float = 1e-4, max_rounds: int = 4, run_seconds: float = 600.0, log=None):
+         tol: float = 1e-4, max_rounds: int = 4, run_seconds: float = 600.0, log=None, ctas_per_sm: int = 0):
     """Tune every class (default: all) for atoms D (K, P, L0, L1) on the
-    device.  make_image(side, seed) returns a device float32 image
+    device, through a queue of the given density (as the server will run it).  make_image(side, seed) returns a device float32 image
     (P, side, side).  Returns {class: {"sub", "stop_margin", "ms", "side",
     "tried": {...}}}."""
     import torch
@@ -96,7 +96,7 @@ def tune(D, make_image, classes=None, margins=(0.99, 0.95, 0.9), reps: int = 2, 
     cur.synchronize()
     table = {}
     with Queue(D, dtd, max_jobs=len(classes) * len(subs) * len(margins) * reps * (max_rounds + 1) + 8,
-               ctl_slots=8, run_seconds=run_seconds) as q:
+               ctl_slots=8, run_seconds=run_seconds, ctas_per_sm=ctas_per_sm) as q:
         for c in classes:
             side = class_side(c)
             beta, Z, ws = bufs[c]

@@ -50,12 +50,15 @@ struct QueueHostSlot {  // pinned host memory, one per job
     unsigned long long t_start;
 };
 
-// Two CTAs of 256 threads (at most 72 registers a thread) per SM: the
-// persistent grid leaves half of every SM's registers, most of its threads and
-// nearly all of its shared memory to the beta-init and refresh kernels of the
-// other streams.
+// CTAs of 256 threads, two or three per SM.  Each SM sub-partition holds
+// 16,384 registers and receives two warps of every CTA:
+//   two CTAs at <= 72 registers a thread hold 9,216 of them and leave room for
+//   the tensor-core beta-init (two warps of <= 104 registers);
+//   three CTAs at <= 64 registers hold 12,288 and leave room only for the FP32
+//   correlations and the refresh kernels (one warp of <= 112 registers);
+// and nearly all of every SM's shared memory stays free for those kernels.
 constexpr int kQueueThreads = 256;
-constexpr int kQueueCtasPerSm = 2;
+constexpr int kQueueCtasPerSmDefault = 2;
 
 // A job-table entry copied to shared memory through L2 (all threads of the
 // CTA, one word each).  The host writes entries while the kernel runs, and
@@ -72,10 +75,12 @@ __device__ __forceinline__ void st_release_sys(int *p, int v) {
     asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// At most 72 registers a thread: two CTAs then hold 9,216 of the 16,384
-// registers of each SM sub-partition, leaving room for the tensor-core
-// beta-init (two warps of at most 104 registers each per sub-partition).
-__global__ void __maxnreg__(72) lgcd_queue_kernel(QueueCtl *qc, QueueJob *jobs, int max_jobs,
+// REGS: the register cap of the grid's density; RB: the worker's row block.
+// Under 64 registers RB = 4 spills about 100 bytes a thread and RB = 2 none,
+// yet RB = 4 served the 512-request trace at 165 solves/s against 134: the
+// loads in flight per unit matter more than the spill traffic.
+template <int REGS, int RB>
+__global__ void __maxnreg__(REGS) lgcd_queue_kernel(QueueCtl *qc, QueueJob *jobs, int max_jobs,
                                                                       QueueHostSlot *host,
                                                                       unsigned long long run_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -134,7 +139,7 @@ __global__ void __maxnreg__(72) lgcd_queue_kernel(QueueCtl *qc, QueueJob *jobs, 
         const int j = s_job;
         stage_l2(&s_args, &jobs[j].a);
         __syncthreads();
-        global_tile_worker<float, kQueueThreads, 4>(s_args, s_tile, smem_raw);
+        global_tile_worker<float, kQueueThreads, RB>(s_args, s_tile, smem_raw);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -169,7 +174,7 @@ struct Queue {
     unsigned char *ctl_pool = nullptr;  // per control slot: header + flag counters
     size_t ctl_stride = 0;
     QueueHostSlot *host = nullptr;
-    int max_jobs = 0, ctl_slots = 0, grid = 0, njobs = 0, next_slot = 0;
+    int max_jobs = 0, ctl_slots = 0, grid = 0, njobs = 0, next_slot = 0, ctas_per_sm = 2;
     std::vector<int> job_ctl;    // control slot of each job (-1 once released)
     std::vector<int> free_ctl;
     csc_solve_opts opts;
@@ -201,14 +206,24 @@ static QueueLayout queue_layout(const Geom &g, int max_jobs, int ctl_slots, int 
     return L;
 }
 
-static int queue_grid() {
+static int queue_grid(int ctas_per_sm) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
         cudaGetLastError();
         sms = 152;
     }
-    return kQueueCtasPerSm * sms;
+    return ctas_per_sm * sms;
+}
+
+// 0 selects the default; anything but 2 or 3 is invalid
+static int queue_density(int ctas_per_sm) {
+    if (ctas_per_sm == 0) return kQueueCtasPerSmDefault;
+    return ctas_per_sm == 2 || ctas_per_sm == 3 ? ctas_per_sm : -1;
+}
+
+static const void *queue_kernel(int ctas_per_sm) {
+    return ctas_per_sm == 3 ? (const void *)lgcd_queue_kernel<64, 4> : (const void *)lgcd_queue_kernel<72, 4>;
 }
 
 static int atoms_geom(const csc_shape *atoms, Geom *g) {
@@ -227,28 +242,32 @@ struct csc_queue : Queue {};
 
 extern "C" {
 
-int csc_queue_workspace_size(const csc_shape *atoms, int max_jobs, int ctl_slots, size_t *device_bytes,
-                             size_t *host_bytes) {
+int csc_queue_workspace_size(const csc_shape *atoms, int max_jobs, int ctl_slots, int ctas_per_sm,
+                             size_t *device_bytes, size_t *host_bytes) {
     Geom g;
     int rc = atoms_geom(atoms, &g);
     if (rc) return rc;
-    if (max_jobs < 1 || ctl_slots < 1 || !device_bytes || !host_bytes) return CSC_ERR_INVALID;
-    const QueueLayout L = queue_layout(g, max_jobs, ctl_slots, queue_grid());
+    const int dens = queue_density(ctas_per_sm);
+    if (max_jobs < 1 || ctl_slots < 1 || dens < 0 || !device_bytes || !host_bytes) return CSC_ERR_INVALID;
+    const QueueLayout L = queue_layout(g, max_jobs, ctl_slots, queue_grid(dens));
     *device_bytes = L.total;
     *host_bytes = L.host;
     return CSC_OK;
 }
 
 int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, const csc_solve_opts *opts,
-                     int max_jobs, int ctl_slots, void *device_ws, size_t device_bytes, void *host_ws,
-                     size_t host_bytes, double run_seconds, csc_stream_t kernel_stream, csc_stream_t side_stream,
-                     csc_queue **out) {
+                     int max_jobs, int ctl_slots, int ctas_per_sm, void *device_ws, size_t device_bytes,
+                     void *host_ws, size_t host_bytes, double run_seconds, csc_stream_t kernel_stream,
+                     csc_stream_t side_stream, csc_queue **out) {
     Geom g;
     int rc = atoms_geom(atoms, &g);
     if (rc) return rc;
-    if (!D || !dtd || !device_ws || !host_ws || !out || max_jobs < 1 || ctl_slots < 1 || !(run_seconds > 0.0))
+    const int dens = queue_density(ctas_per_sm);
+    if (!D || !dtd || !device_ws || !host_ws || !out || max_jobs < 1 || ctl_slots < 1 || dens < 0 ||
+        !(run_seconds > 0.0))
         return CSC_ERR_INVALID;
-    const int grid = queue_grid();
+    const int grid = queue_grid(dens);
+    const void *kern = queue_kernel(dens);
     const QueueLayout L = queue_layout(g, max_jobs, ctl_slots, grid);
     if (device_bytes < L.total || host_bytes < L.host) return CSC_ERR_WORKSPACE;
     // Both streams must be non-blocking: work on the legacy default stream
@@ -268,7 +287,7 @@ int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, c
     // otherwise the beta-init and refresh kernels, which need tens of KB,
     // could not start on any SM until the queue closes.
     {
-        cudaError_t e = cudaFuncSetAttribute(lgcd_queue_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                              (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return set_cuda_error(e);
     }
@@ -292,6 +311,7 @@ int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, c
     q->max_jobs = max_jobs;
     q->ctl_slots = ctl_slots;
     q->grid = grid;
+    q->ctas_per_sm = dens;
     for (int i = ctl_slots - 1; i >= 0; i--) q->free_ctl.push_back(i);
     csc_default_opts(&q->opts);
     if (opts) q->opts = *opts;
@@ -313,9 +333,13 @@ int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, c
     }
     if ((e = cudaStreamSynchronize(ss)) != cudaSuccess) return fail(e);
     const size_t smem = 2 * (size_t)g.K * sizeof(float);
-    lgcd_queue_kernel<<<grid, kQueueThreads, smem, q->kstream>>>(q->qc, q->jobs, max_jobs, q->host,
-                                                                  (unsigned long long)(run_seconds * 1e9));
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    QueueCtl *qc = q->qc;
+    QueueJob *jobs = q->jobs;
+    QueueHostSlot *host = q->host;
+    unsigned long long run_ns = (unsigned long long)(run_seconds * 1e9);
+    void *args[] = {&qc, &jobs, &max_jobs, &host, &run_ns};
+    if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(kQueueThreads), args, smem, q->kstream)) != cudaSuccess)
+        return fail(e);
     *out = q;
     return CSC_OK;
 }

@@ -122,7 +122,8 @@ class Server:
 
     def __init__(self, D, hbm_budget: int, max_side=(2048, 2048), reg: float = 0.1, tol: float = 1e-4,
                  precision: str = "fp32", max_jobs: int = 8192, ctl_slots: int = 256,
-                 run_seconds: float = 600.0, max_rounds: int = 4, tuning: dict | None = None):
+                 run_seconds: float = 600.0, max_rounds: int = 4, tuning: dict | None = None,
+                 ctas_per_sm: int | None = None):
         import torch
         if precision not in ("fp32", "bf16x3"):
             raise ValueError("precision must be 'fp32' or 'bf16x3'")
@@ -146,7 +147,13 @@ class Server:
             _, self.dtd, _ = csc_init_beta(x0, D, ws=self.ws, stream=self.stream)
             self.dtd_scratch = torch.empty_like(self.dtd)
         self.stream.synchronize()
-        self.q = Queue(D, self.dtd, max_jobs=max_jobs, ctl_slots=ctl_slots, run_seconds=run_seconds)
+        # three queue CTAs per SM when only FP32 kernels run beside it, two
+        # when the tensor-core beta-init must fit too
+        if ctas_per_sm is None:
+            ctas_per_sm = 3 if precision == "fp32" else 2
+        self.ctas_per_sm = ctas_per_sm
+        self.q = Queue(D, self.dtd, max_jobs=max_jobs, ctl_slots=ctl_slots, run_seconds=run_seconds,
+                       ctas_per_sm=ctas_per_sm)
         self.active = {}
         self.n_free_ctl = ctl_slots
 

@@ -173,3 +173,26 @@ def test_queue_degenerate_and_thin_images(pkg):
         assert st["status"] == 0
         ref = pkg.csc_objective(r.X, Dd, Z, float(np.float32(r.lam)))
         assert abs(obj - ref) <= REL * abs(ref) + 1e-9, (tuple(r.X.shape), obj, ref)
+
+
+def test_queue_three_ctas_per_sm(pkg):
+    """The denser grid (three CTAs per SM) with the FP32 beta-init and refresh
+    beside it gives the same results as single solves; densities other than 2
+    or 3 are refused."""
+    D = _atoms(23)
+    Dd = dev(D)
+    reqs = [_Req(pkg, _image(s0, s1, 90 + i, D), Dd) for i, (s0, s1) in enumerate([(300, 260), (96, 128), (700, 650)])]
+    with pkg.Queue(Dd, reqs[0].dtd, max_jobs=64, ctl_slots=16, run_seconds=60.0, ctas_per_sm=3) as q:
+        jobs = [q.submit(r.beta, r.Z, r.lam, TOL) for r in reqs]
+        # an FP32 beta-init beside the running queue (the refreshes below too)
+        extra = _Req(pkg, _image(200, 200, 99, D), Dd)
+        objs = [_finish(pkg, q, r, Dd, j)[0] for r, j in zip(reqs, jobs)]
+        obj_x = _finish(pkg, q, extra, Dd, q.submit(extra.beta, extra.Z, extra.lam, TOL))[0]
+    for r, obj in zip(reqs + [extra], objs + [obj_x]):
+        beta, _, _ = pkg.csc_init_beta(r.X, Dd)
+        Z, st = pkg.csc_lgcd_solve(r.X, Dd, r.dtd, beta, r.lam, TOL)
+        ref = pkg.csc_objective(r.X, Dd, Z, float(np.float32(r.lam)))
+        assert abs(obj - ref) <= REL * abs(ref)
+    with pytest.raises(pkg.CscError) as e:
+        pkg.Queue(Dd, reqs[0].dtd, max_jobs=4, ctl_slots=2, ctas_per_sm=5)
+    assert e.value.status == pkg.CSC_ERR_INVALID
