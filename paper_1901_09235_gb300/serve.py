@@ -151,6 +151,8 @@ class Server:
         # when the tensor-core beta-init must fit too
         if ctas_per_sm is None:
             ctas_per_sm = 3 if precision == "fp32" else 2
+        if precision == "bf16x3" and ctas_per_sm == 3:
+            raise ValueError("the tensor-core beta-init does not fit beside a queue of three CTAs per SM")
         self.ctas_per_sm = ctas_per_sm
         self.q = Queue(D, self.dtd, max_jobs=max_jobs, ctl_slots=ctl_slots, run_seconds=run_seconds,
                        ctas_per_sm=ctas_per_sm)
