@@ -87,3 +87,30 @@ def test_null_pointers_rejected(lib):
                             C.byref(st), None)
     assert rc == pkg.CSC_ERR_INVALID
     assert lib.cdl_dict_stats(C.byref(s), None, None, None, None, None, 0, None) == pkg.CSC_ERR_INVALID
+
+
+def test_option_and_queue_arguments_rejected_on_host(lib):
+    """Out-of-range solve options and queue densities are refused before any
+    device work (the pointers below are never dereferenced)."""
+    import paper_1901_09235_gb300 as pkg
+    s = pkg.make_shape((2, 100), (3, 2, 5))
+    st = pkg.SolveStats()
+    fake = [C.c_void_p(16 * (i + 1)) for i in range(6)]
+    for bad in (-0.1, 1.5, float("nan")):
+        o = pkg.default_opts(stop_margin=bad)
+        rc = lib.csc_lgcd_solve(C.byref(s), fake[0], fake[1], fake[2], fake[3], fake[4], 0.1, 1e-4,
+                                C.byref(o), fake[5], 1 << 30, C.byref(st), None)
+        assert rc == pkg.CSC_ERR_INVALID, bad
+    atoms = pkg.Shape()
+    atoms.d, atoms.P, atoms.K = 2, 3, 16
+    atoms.T[0] = atoms.T[1] = atoms.L[0] = atoms.L[1] = 12
+    db, hb = C.c_size_t(0), C.c_size_t(0)
+    for dens in (1, 4, -2):
+        assert lib.csc_queue_workspace_size(C.byref(atoms), 8, 4, dens, C.byref(db), C.byref(hb)) == \
+            pkg.CSC_ERR_INVALID
+    sizes = []
+    for dens in (0, 2, 3):
+        assert lib.csc_queue_workspace_size(C.byref(atoms), 8, 4, dens, C.byref(db), C.byref(hb)) == pkg.CSC_OK
+        sizes.append(db.value)
+    # the default is two CTAs per SM; three need larger per-slot control areas
+    assert sizes[0] == sizes[1] < sizes[2]
