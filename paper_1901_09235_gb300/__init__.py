@@ -440,6 +440,15 @@ class Queue:
     def __exit__(self, *exc):
         self.close()
 
+    def __del__(self):
+        # a queue dropped without close() would keep its kernel running until
+        # run_seconds; stop it (best effort: the CUDA context may already be gone)
+        try:
+            if getattr(self, "_h", None) is not None:
+                self.close()
+        except Exception:
+            pass
+
 
 def cdl_dict_stats(Z, X, D_shape, phi=None, psi=None, ws=None, stream=None):
     """phi = Z~ * Z on Phi and psi = Z~ * X on Theta (cdl_dict_stats)."""
