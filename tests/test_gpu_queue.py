@@ -196,3 +196,22 @@ def test_queue_three_ctas_per_sm(pkg):
     with pytest.raises(pkg.CscError) as e:
         pkg.Queue(Dd, reqs[0].dtd, max_jobs=4, ctl_slots=2, ctas_per_sm=5)
     assert e.value.status == pkg.CSC_ERR_INVALID
+
+
+def test_dropped_queue_stops_its_kernel(pkg):
+    """A queue that goes out of scope without close() ends its persistent
+    kernel at once, not after run_seconds."""
+    import gc
+    import time
+    D = _atoms()
+    Dd = dev(D)
+    r = _Req(pkg, _image(40, 40, 11, D), Dd)
+    q = pkg.Queue(Dd, r.dtd, max_jobs=8, ctl_slots=4, run_seconds=30.0)
+    st = q.wait(q.submit(r.beta, r.Z, r.lam, TOL))
+    assert st["status"] == 0
+    ks = q.kernel_stream
+    del q
+    gc.collect()
+    t0 = time.monotonic()
+    ks.synchronize()  # returns by run_seconds at the latest
+    assert time.monotonic() - t0 < 5.0
