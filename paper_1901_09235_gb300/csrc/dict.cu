@@ -272,7 +272,7 @@ struct PgdArgs {
     const float *phi, *psi;
     float *D;      // in/out
     float *qd, *qg;  // per-CTA scratch: [cluster rank][K sources][ka * per]
-    double *out;   // [objective, iterations, eta]
+    double *out;   // [objective, iterations, eta, Armijo trials, phase cycles x 6]
     double x_sqnorm, tol;
     int K, P, L0, L1, max_iter, ka, stage_phi, q_in_smem;
 };
@@ -280,6 +280,8 @@ struct PgdArgs {
 constexpr int kPgdThreads = 512;
 constexpr int kPgdWarps = kPgdThreads / 32;
 constexpr int kPgdMaxK = 32;
+constexpr int kPgdTrialWarps = 4;  // Armijo trials evaluated at once
+constexpr int kPgdMaxCluster = 16;  // CTAs of the cluster, at most
 constexpr float kPgdMinTol = 4.0f / 16777216.0f;  // 4 x 2^-24
 
 // Block-wide sum returned to every thread (warp 0 combines the warp sums).
@@ -294,6 +296,66 @@ __device__ __forceinline__ double block_reduce_sum(double v, double *scratch) {
     }
     __syncthreads();
     return scratch[kPgdWarps];
+}
+
+// One group of NP channels of conv_per_source: lane positions o0 and o1
+// (valid when v0 / v1), phi row ph of the (k, k2) pair, source rows sv.
+// NP is a template argument so that no FMA of an absent channel is issued.
+template <int NP>
+__device__ __forceinline__ void conv_channels(const float *__restrict__ ph, const float *__restrict__ sv, int LL,
+                                              int L0, int L1, int W1, int base0, int base1, bool v0, bool v1,
+                                              float *__restrict__ dst, int o0, int o1) {
+    float acc0[NP], acc1[NP];
+#pragma unroll
+    for (int j = 0; j < NP; j++) acc0[j] = acc1[j] = 0.f;
+    for (int a2 = 0; a2 < L0; a2++) {
+        const float *__restrict__ srow = sv + a2 * L1;
+        const int off = a2 * W1;
+        int b2 = 0;
+        if ((LL & 3) == 0 && (L1 & 3) == 0) {
+            // four taps at a time: the source values of every channel as one
+            // 16-byte load each, the eight phi values, then the products; two
+            // groups in flight (up to five channels, within the register cap) so
+            // that the loads of one overlap the other's FMAs
+#pragma unroll(NP <= 5 ? 2 : 1)
+            for (; b2 < L1; b2 += 4) {
+                float f0[4], f1[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    f0[u] = v0 ? ph[base0 - off - b2 - u] : 0.f;
+                    f1[u] = v1 ? ph[base1 - off - b2 - u] : 0.f;
+                }
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    const float4 g = *reinterpret_cast<const float4 *>(srow + (size_t)j * LL + b2);
+                    acc0[j] = fmaf(f0[0], g.x, acc0[j]);
+                    acc1[j] = fmaf(f1[0], g.x, acc1[j]);
+                    acc0[j] = fmaf(f0[1], g.y, acc0[j]);
+                    acc1[j] = fmaf(f1[1], g.y, acc1[j]);
+                    acc0[j] = fmaf(f0[2], g.z, acc0[j]);
+                    acc1[j] = fmaf(f1[2], g.z, acc1[j]);
+                    acc0[j] = fmaf(f0[3], g.w, acc0[j]);
+                    acc1[j] = fmaf(f1[3], g.w, acc1[j]);
+                }
+            }
+        }
+#pragma unroll 4
+        for (; b2 < L1; b2++) {
+            const float f0 = v0 ? ph[base0 - off - b2] : 0.f;
+            const float f1 = v1 ? ph[base1 - off - b2] : 0.f;
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                const float g = srow[(size_t)j * LL + b2];
+                acc0[j] = fmaf(f0, g, acc0[j]);
+                acc1[j] = fmaf(f1, g, acc1[j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NP; j++) {
+        if (v0) dst[(size_t)j * LL + o0] = acc0[j];
+        if (v1) dst[(size_t)j * LL + o1] = acc1[j];
+    }
 }
 
 // out[k2][e] = sum_tau2 phi_{k,k2}[tau - tau2] src[k2][p][tau2] for the own
@@ -322,61 +384,20 @@ __device__ __forceinline__ void conv_per_source(const PgdArgs &a, const float *s
         const int base1 = v1 ? (o1 / a.L1 + a.L0 - 1) * W1 + o1 % a.L1 + a.L1 - 1 : 0;
         float *__restrict__ dst = out + (size_t)k2 * own_cap + (size_t)kl * per;
         for (int pc = 0; pc < a.P; pc += 8) {
-            const int np = min(8, a.P - pc);
-            float acc0[8], acc1[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) acc0[j] = acc1[j] = 0.f;
-            for (int a2 = 0; a2 < a.L0; a2++) {
-                const float *__restrict__ srow = sv + (size_t)pc * LL + a2 * a.L1;
-                const int off = a2 * W1;
-                int b2 = 0;
-                if ((LL & 3) == 0 && (a.L1 & 3) == 0) {
-                    // four taps at a time: the source values of every channel as one
-                    // 16-byte load each, the eight phi values, then the products
-                    for (; b2 < a.L1; b2 += 4) {
-                        float f0[4], f1[4];
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            f0[u] = v0 ? ph[base0 - off - b2 - u] : 0.f;
-                            f1[u] = v1 ? ph[base1 - off - b2 - u] : 0.f;
-                        }
-#pragma unroll
-                        for (int j = 0; j < 8; j++) {
-                            if (j < np) {
-                                const float4 g = *reinterpret_cast<const float4 *>(srow + (size_t)j * LL + b2);
-                                acc0[j] = fmaf(f0[0], g.x, acc0[j]);
-                                acc1[j] = fmaf(f1[0], g.x, acc1[j]);
-                                acc0[j] = fmaf(f0[1], g.y, acc0[j]);
-                                acc1[j] = fmaf(f1[1], g.y, acc1[j]);
-                                acc0[j] = fmaf(f0[2], g.z, acc0[j]);
-                                acc1[j] = fmaf(f1[2], g.z, acc1[j]);
-                                acc0[j] = fmaf(f0[3], g.w, acc0[j]);
-                                acc1[j] = fmaf(f1[3], g.w, acc1[j]);
-                            }
-                        }
-                    }
-                }
-#pragma unroll 4
-                for (; b2 < a.L1; b2++) {
-                    const float f0 = v0 ? ph[base0 - off - b2] : 0.f;
-                    const float f1 = v1 ? ph[base1 - off - b2] : 0.f;
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        if (j < np) {
-                            const float g = srow[(size_t)j * LL + b2];
-                            acc0[j] = fmaf(f0, g, acc0[j]);
-                            acc1[j] = fmaf(f1, g, acc1[j]);
-                        }
-                    }
-                }
+            const float *s = sv + (size_t)pc * LL;
+            float *d = dst + (size_t)pc * LL;
+#define PGD_CONV(NP) conv_channels<NP>(ph, s, LL, a.L0, a.L1, W1, base0, base1, v0, v1, d, o0, o1)
+            switch (min(8, a.P - pc)) {
+                case 1: PGD_CONV(1); break;
+                case 2: PGD_CONV(2); break;
+                case 3: PGD_CONV(3); break;
+                case 4: PGD_CONV(4); break;
+                case 5: PGD_CONV(5); break;
+                case 6: PGD_CONV(6); break;
+                case 7: PGD_CONV(7); break;
+                default: PGD_CONV(8); break;
             }
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                if (j < np) {
-                    if (v0) dst[(size_t)(pc + j) * LL + o0] = acc0[j];
-                    if (v1) dst[(size_t)(pc + j) * LL + o1] = acc1[j];
-                }
-            }
+#undef PGD_CONV
         }
     }
 }
@@ -392,14 +413,10 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     const int own_cap = a.ka * per;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // dynamic shared memory; every CTA holds the full G and every atom's
-    // scalars / Gram rows, written by their owners before a cluster barrier
-    double *sa = reinterpret_cast<double *>(smem_raw), *sb = sa + K, *sc = sb + K;
-    const int rowlen = 3 + 3 * K;
-    double *allsc = sc + K;                       // [K][rowlen]
-    // the float section starts on a 16-byte boundary (vector loads of G)
-    const size_t dbytes = ((3 * (size_t)K + (size_t)K * rowlen) * sizeof(double) + 15) & ~(size_t)15;
-    float *gall = reinterpret_cast<float *>(smem_raw + dbytes);
+    // dynamic shared memory; every CTA holds the full G (the static arrays
+    // below hold every atom's scalars and Gram rows, written by their owners
+    // before a cluster barrier)
+    float *gall = reinterpret_cast<float *>(smem_raw);
     float *sD = gall + n, *sG = sD + own_cap;
     float *sphi = sG + own_cap;
     float *qsm = sphi + (a.stage_phi ? (size_t)a.ka * K * WW : 0);
@@ -411,6 +428,8 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     __shared__ float fsa[kPgdMaxK], fsa1[kPgdMaxK], fsb[kPgdMaxK], fsc[kPgdMaxK];
     __shared__ float fMDD[kPgdMaxK * kPgdMaxK], fMDG[kPgdMaxK * kPgdMaxK], fMGG[kPgdMaxK * kPgdMaxK];
     __shared__ double s_ctl[4];  // eta, dsq, dnorm, stop
+    __shared__ int s_pass[2][kPgdTrialWarps];  // Armijo test per trial, by round parity
+    __shared__ float s_ta[kPgdTrialWarps][kPgdMaxK], s_tb[kPgdTrialWarps][kPgdMaxK];  // per-trial alpha, beta
     __shared__ double s_lip;
 
     // stage own slices and phi rows; the full D is the first convolution input
@@ -443,36 +462,48 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
     double lip = 0.0;
     for (int r = 0; r < ncl; r++) lip = fmax(lip, *cl.map_shared_rank(&s_lip, (unsigned)r));
 
+    // SM cycles per phase, kept by thread 0 in shared memory (no registers)
+    __shared__ unsigned long long s_ph[6], s_tc;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 6; i++) s_ph[i] = 0;
+        s_tc = clock64();
+    }
+#define PGD_TICK(i)                              \
+    if (threadIdx.x == 0) {                      \
+        const unsigned long long tn_ = clock64(); \
+        s_ph[i] += tn_ - s_tc;                   \
+        s_tc = tn_;                              \
+    }
     // QG = phi * G per source, then the own atoms' scalars and Gram rows,
     // written to every CTA; after the barrier they are read locally
-    unsigned long long ph[6] = {0, 0, 0, 0, 0, 0}, tc = clock64(), tn;
-#define PGD_TICK(i)      \
-    tn = clock64();      \
-    ph[i] += tn - tc;    \
-    tc = tn;
     auto refresh_stats = [&]() {
         conv_per_source(a, sphi, k_lo, nk, gall, qg, own_cap);
         __syncthreads();
         PGD_TICK(4)
-        // rows: warp w handles (own atom kl, item i) pairs; item 0 = the three
-        // FP64 scalars, items 1..K = the Gram entries of source k2 = i - 1
-        for (int q = warp; q < nk * (K + 1); q += kPgdWarps) {
-            const int kl = q / (K + 1), i = q - kl * (K + 1);
+        // warp w handles (own atom kl, item i) pairs: items 0..2 = the FP64
+        // scalars ||D_k||^2, <D_k, G_k>, ||G_k||^2; items 3..K+2 = the Gram
+        // entries of source k2 = i - 3.  Lanes 0 .. ncl-1 store the FP32 values
+        // straight into one CTA each; the cluster barrier publishes them, and
+        // no CTA reads them before its next Armijo step
+        for (int q = warp; q < nk * (K + 3); q += kPgdWarps) {
+            const int kl = q / (K + 3), i = q - kl * (K + 3);
+            const int k = k_lo + kl;
             const float *d = sD + (size_t)kl * per, *g = sG + (size_t)kl * per;
-            double v0, v1, v2;
-            if (i == 0) {
-                double x0 = 0.0, x1 = 0.0, x2 = 0.0;
-                for (int e = lane; e < per; e += 32) {
-                    const double dv = d[e], gv = g[e];
-                    x0 = fma(dv, dv, x0);
-                    x1 = fma(dv, gv, x1);
-                    x2 = fma(gv, gv, x2);
+            if (i < 3) {
+                const float *x = i == 2 ? g : d, *y = i == 0 ? d : g;
+                double acc = 0.0;
+                for (int e = lane; e < per; e += 32) acc = fma((double)x[e], (double)y[e], acc);
+                acc = warp_sum(acc);
+                for (int r = lane; r < ncl; r += 32) {
+                    if (i == 0) {
+                        cl.map_shared_rank(fsa, (unsigned)r)[k] = (float)acc;
+                        cl.map_shared_rank(fsa1, (unsigned)r)[k] = (float)(acc - 1.0);  // before rounding
+                    } else {
+                        cl.map_shared_rank(i == 1 ? fsb : fsc, (unsigned)r)[k] = (float)acc;
+                    }
                 }
-                v0 = warp_sum(x0);
-                v1 = warp_sum(x1);
-                v2 = warp_sum(x2);
             } else {
-                const int k2 = i - 1;
+                const int k2 = i - 3;
                 const float *qdr = qd + (size_t)k2 * own_cap + (size_t)kl * per;
                 const float *qgr = qg + (size_t)k2 * own_cap + (size_t)kl * per;
                 float dd = 0.f, dg = 0.f, gg = 0.f;
@@ -486,50 +517,19 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
                     dg += __shfl_xor_sync(0xffffffffu, dg, o);
                     gg += __shfl_xor_sync(0xffffffffu, gg, o);
                 }
-                v0 = dd;
-                v1 = dg;
-                v2 = gg;
-            }
-            // lanes 0 .. ncl-1 write the three values to one CTA each
-            const int k = k_lo + kl;
-            for (int r = lane; r < ncl; r += 32) {
-                double *dst = cl.map_shared_rank(allsc, (unsigned)r) + (size_t)k * rowlen;
-                if (i == 0) {
-                    dst[0] = v0;
-                    dst[1] = v1;
-                    dst[2] = v2;
-                } else {
-                    dst[3 + (i - 1)] = v0;
-                    dst[3 + K + (i - 1)] = v1;
-                    dst[3 + 2 * K + (i - 1)] = v2;
+                for (int r = lane; r < ncl; r += 32) {
+                    cl.map_shared_rank(fMDD, (unsigned)r)[k * K + k2] = dd;
+                    cl.map_shared_rank(fMDG, (unsigned)r)[k * K + k2] = dg;
+                    cl.map_shared_rank(fMGG, (unsigned)r)[k * K + k2] = gg;
                 }
             }
         }
         cl.sync();
-        for (int q = threadIdx.x; q < K * rowlen; q += kPgdThreads) {
-            const int k = q / rowlen, i = q - k * rowlen;
-            const double v = allsc[q];
-            if (i == 0) {
-                sa[k] = v;
-                fsa[k] = (float)v;
-                fsa1[k] = (float)(v - 1.0);  // ||D_k||^2 - 1 before rounding
-            } else if (i == 1) {
-                sb[k] = v;
-                fsb[k] = (float)v;
-            } else if (i == 2) {
-                sc[k] = v;
-                fsc[k] = (float)v;
-            }
-            else if (i < 3 + K) fMDD[k * K + (i - 3)] = (float)v;
-            else if (i < 3 + 2 * K) fMDG[k * K + (i - 3 - K)] = (float)v;
-            else fMGG[k * K + (i - 3 - 2 * K)] = (float)v;
-        }
-        __syncthreads();
     };
     refresh_stats();
 
     double eta = lip > 0.0 ? 1.0 / lip : 0.0;
-    int it = 0;
+    int it = 0, n_trials = 0;
     if (lip > 0.0) {
         for (it = 0; it < a.max_iter; it++) {
             // Armijo backtracking by warp 0 on the per-atom scalars, in FP32:
@@ -537,54 +537,73 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
             // - 2 eta <D_k, G_k> + eta^2 ||G_k||^2 (the first term taken from the
             // FP64 sum) and s_k = 1 / sqrt(1 + delta_k), the scale deviation
             // s_k - 1 = -delta_k s_k^2 / (1 + s_k) has no cancellation
-            if (threadIdx.x < 32) {
-                float e_try = it > 0 ? 2.0f * (float)eta : (float)eta, dsq = 0.f, dnorm = 0.f;
-                {
-                    float dn = 0.f;
-                    for (int k = lane; k < K; k += 32) dn += fsa[k];
-                    for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
-                    dnorm = dn;
-                }
-                for (int bt = 0; bt < 60; bt++) {
-                    float ds = 0.f;
-                    for (int k = lane; k < K; k += 32) {
-                        const float delta = fsa1[k] + e_try * (e_try * fsc[k] - 2.0f * fsb[k]);
-                        float sk = 1.f, al = 0.f;
-                        if (delta > 0.f) {
-                            float r = rsqrtf(1.f + delta);
-                            r = r * (1.5f - 0.5f * (1.f + delta) * r * r);  // one Newton step
-                            sk = r;
-                            al = -delta * r * r / (1.f + r);
-                        }
-                        const float be = -sk * e_try;
-                        ds += al * (al * fsa[k] + 2.f * be * fsb[k]) + be * be * fsc[k];
-                        s_scale[k] = sk;
-                        s_alpha[k] = al;
-                        s_beta[k] = be;
+            // Lane k holds atom k (K <= 32).  The backtracking trials
+            // eta_t = eta_0 2^-t run kPgdTrialWarps at a time, trial t on warp
+            // t mod kPgdTrialWarps, each with its own alpha / beta scratch; the
+            // first trial that passes is taken, with the same arithmetic as if
+            // they ran one after another.
+            if (warp < kPgdTrialWarps) {
+                const bool own = lane < K;
+                const float ak = own ? fsa[lane] : 0.f, a1k = own ? fsa1[lane] : 0.f;
+                const float bk = own ? fsb[lane] : 0.f, ck = own ? fsc[lane] : 0.f;
+                const float e0 = it > 0 ? 2.0f * (float)eta : (float)eta;
+                for (int t0 = 0;; t0 += kPgdTrialWarps) {
+                    const int t = t0 + warp;
+                    const float e_try = ldexpf(e0, -t);  // exact halvings
+                    const float delta = a1k + e_try * (e_try * ck - 2.0f * bk);
+                    float sk = 1.f, al = 0.f;
+                    if (own && delta > 0.f) {
+                        float r = rsqrtf(1.f + delta);
+                        r = r * (1.5f - 0.5f * (1.f + delta) * r * r);  // one Newton step
+                        sk = r;
+                        al = -delta * r * r / (1.f + r);
+                    }
+                    const float be = own ? -sk * e_try : 0.f;
+                    float ds = al * (al * ak + 2.f * be * bk) + be * be * ck;
+                    // <D+ - D, phi * (D+ - D)> from the Gram entries
+                    float *ta = s_ta[warp], *tb = s_tb[warp];
+                    if (own) {
+                        ta[lane] = al;
+                        tb[lane] = be;
                     }
                     __syncwarp();
                     float qf = 0.f;
                     for (int q = lane; q < K * K; q += 32) {
-                        const int k = q / K, k2 = q % K;
-                        const float al = s_alpha[k], be = s_beta[k], al2 = s_alpha[k2], be2 = s_beta[k2];
-                        qf += al * (al2 * fMDD[q] + be2 * fMDG[q]) + be * (al2 * fMDG[k2 * K + k] + be2 * fMGG[q]);
+                        const int k = q / K, k2 = q - k * K;
+                        const float alk = ta[k], bek = tb[k], al2 = ta[k2], be2 = tb[k2];
+                        qf += alk * (al2 * fMDD[q] + be2 * fMDG[q]) + bek * (al2 * fMDG[k2 * K + k] + be2 * fMGG[q]);
                     }
                     for (int o = 16; o > 0; o >>= 1) {
                         qf += __shfl_xor_sync(0xffffffffu, qf, o);
                         ds += __shfl_xor_sync(0xffffffffu, ds, o);
                     }
-                    dsq = ds;
-                    if (qf * e_try <= dsq || bt == 59) break;
-                    e_try *= 0.5f;
-                    __syncwarp();
-                }
-                if (lane == 0) {
-                    s_ctl[0] = e_try;
-                    s_ctl[1] = dsq;
-                    s_ctl[2] = dnorm;
-                    // a relative change below the FP32 resolution of D is noise
-                    const float tol = fmaxf((float)a.tol, kPgdMinTol);
-                    s_ctl[3] = sqrtf(dsq) < tol * sqrtf(dnorm) ? 1.0 : 0.0;
+                    const int par = (t0 / kPgdTrialWarps) & 1;
+                    if (lane == 0) s_pass[par][warp] = (qf * e_try <= ds || t >= 59) ? 1 : 0;
+                    asm volatile("bar.sync 2, %0;" ::"r"(kPgdTrialWarps * 32) : "memory");
+                    int win = -1;
+#pragma unroll
+                    for (int w = kPgdTrialWarps - 1; w >= 0; w--)
+                        if (s_pass[par][w]) win = w;
+                    if (win < 0) continue;  // every trial of this round failed
+                    if (threadIdx.x == 0) n_trials += t0 + win + 1;
+                    if (warp == win) {
+                        if (own) {
+                            s_scale[lane] = sk;
+                            s_alpha[lane] = al;
+                            s_beta[lane] = be;
+                        }
+                        float dnorm = ak;
+                        for (int o = 16; o > 0; o >>= 1) dnorm += __shfl_xor_sync(0xffffffffu, dnorm, o);
+                        if (lane == 0) {
+                            s_ctl[0] = e_try;
+                            s_ctl[1] = ds;
+                            s_ctl[2] = dnorm;
+                            // a relative change below the FP32 resolution of D is noise
+                            const float tol = fmaxf((float)a.tol, kPgdMinTol);
+                            s_ctl[3] = sqrtf(ds) < tol * sqrtf(dnorm) ? 1.0 : 0.0;
+                        }
+                    }
+                    break;
                 }
             }
             __syncthreads();
@@ -645,7 +664,8 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
         a.out[0] = 0.5 * a.x_sqnorm - 0.5 * tp + 0.5 * tg;
         a.out[1] = (double)it;
         a.out[2] = eta;
-        for (int i = 0; i < 6; i++) a.out[4 + i] = (double)ph[i];
+        a.out[3] = (double)n_trials;
+        for (int i = 0; i < 6; i++) a.out[4 + i] = (double)s_ph[i];
     }
     cl.sync();  // keep every rank's shared memory alive until all reads are done
 }
@@ -653,12 +673,11 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
 
 static size_t pgd_smem(const Geom &g, int ka, bool stage, bool qsm) {
     const long long per = (long long)g.P * g.L0 * g.L1, n = g.nd();
-    const int K = g.K, rowlen = 3 + 3 * K;
-    size_t d = ((3 * (size_t)K + (size_t)K * rowlen) * sizeof(double) + 15) & ~(size_t)15;
+    const int K = g.K;
     size_t f = ((size_t)n + 2 * (size_t)ka * per + (stage ? (size_t)ka * K * g.nw() : 0) +
                 (qsm ? 2 * (size_t)K * ka * per : 0)) *
                sizeof(float);
-    return d + f;
+    return f;
 }
 
 int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x_sqnorm, float *D,
@@ -708,7 +727,7 @@ int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x
         CSC_CUDA(cudaFuncSetAttribute(pgd_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         bool ok = false;
         Choice ch{dev, g.K, g.P, g.L0, g.L1, 0, 0, 0, 0};
-        for (int ka = (int)ceil_div(g.K, 16); ka <= g.K && !ok; ka++) {
+        for (int ka = (int)ceil_div(g.K, kPgdMaxCluster); ka <= g.K && !ok; ka++) {
             const int cs = (int)ceil_div(g.K, ka);
             if (pgd_smem(g, ka, false, false) > lim) break;
             ch.ka = ka;
