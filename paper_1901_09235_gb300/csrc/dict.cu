@@ -560,6 +560,7 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
                     }
                     const float be = own ? -sk * e_try : 0.f;
                     float ds = al * (al * ak + 2.f * be * bk) + be * be * ck;
+                    float da = al * al * ak + fabsf(2.f * al * be * bk) + be * be * ck;  // |terms|
                     // <D+ - D, phi * (D+ - D)> from the Gram entries
                     float *ta = s_ta[warp], *tb = s_tb[warp];
                     if (own) {
@@ -576,6 +577,7 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
                     for (int o = 16; o > 0; o >>= 1) {
                         qf += __shfl_xor_sync(0xffffffffu, qf, o);
                         ds += __shfl_xor_sync(0xffffffffu, ds, o);
+                        da += __shfl_xor_sync(0xffffffffu, da, o);
                     }
                     const int par = (t0 / kPgdTrialWarps) & 1;
                     if (lane == 0) s_pass[par][warp] = (qf * e_try <= ds || t >= 59) ? 1 : 0;
@@ -598,9 +600,16 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
                             s_ctl[0] = e_try;
                             s_ctl[1] = ds;
                             s_ctl[2] = dnorm;
-                            // a relative change below the FP32 resolution of D is noise
+                            // stop when ||D+ - D|| < tol ||D|| (a relative change below
+                            // the FP32 resolution of D is noise), or when the computed
+                            // ||D+ - D||^2 lies within its own rounding bound, 2 gamma_{K+3}
+                            // times the sum of its terms' magnitudes: near a solution with
+                            // active norm constraints alpha_k D_k and beta_k G_k cancel, and
+                            // below that level the FP32 scalars no longer resolve the change
+                            // (the test that follows it would then take steps blindly)
                             const float tol = fmaxf((float)a.tol, kPgdMinTol);
-                            s_ctl[3] = sqrtf(ds) < tol * sqrtf(dnorm) ? 1.0 : 0.0;
+                            const float floor_ds = 2.f * (float)(K + 3) * 5.96e-8f * da;
+                            s_ctl[3] = (sqrtf(fmaxf(ds, 0.f)) < tol * sqrtf(dnorm) || ds <= floor_ds) ? 1.0 : 0.0;
                         }
                     }
                     break;

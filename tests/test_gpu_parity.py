@@ -212,6 +212,24 @@ def test_dict_update(pkg, orc, w):
     assert 1 <= it <= 50 and 1 <= it_ref <= 50
 
 
+@pytest.mark.parametrize("w", [W_1D, W_2D], ids=["1d", "2d"])
+def test_dict_update_from_the_generating_atoms(pkg, orc, w):
+    """Started from the unit-norm atoms that generated X (norm constraints
+    active near the solution, as in the CDL loop), the FP32 step stops by its
+    own tests before the iteration cap and its cost is within 10^-6
+    (relative) of the FP64 oracle's."""
+    X, D, Z = make_problem(w, 31)
+    phi, psi = orc.phi_psi(Z, X, w.L)
+    phi32, psi32 = phi.astype(np.float32), psi.astype(np.float32)
+    xs = float(np.sum(X.astype(np.float64) ** 2))
+    Dd = dev(D)
+    _, it = pkg.cdl_dict_update(dev(phi32), dev(psi32), xs, Dd, X.shape, max_iter=50, tol=1e-8)
+    _, f_ref, it_ref = orc.pgd_armijo(phi32, psi32, xs, D, max_iter=50, tol=1e-8)
+    f_d = orc.dict_objective(phi32, psi32, xs, host(Dd))
+    assert it < 50, (it, it_ref)
+    assert f_d - f_ref <= 1e-6 * abs(f_ref), (f_d, f_ref, it, it_ref)
+
+
 @pytest.mark.parametrize("w", ASYNC, ids=[w.name for w in ASYNC])
 def test_async_global_tiles_match_oracle(pkg, orc, w):
     """The global-memory variant (beta, Z in HBM, atomic window updates,
