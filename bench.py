@@ -5,7 +5,8 @@ multichannel workload (P = 5, T = 200,000, K = 10 atoms of L = 64):
   csc_init_beta (beta = D~ * X, the D^T D table, lambda_max)
   csc_lgcd_solve (LGCD with soft-locks to max |dZ| < 1e-4, lambda = 0.1 lambda_max,
                   FP64 objective and KKT on a beta recomputed from scratch)
-  cdl_dict_stats (phi, psi) and cdl_dict_update (PGD + Armijo on D).
+  cdl_dict_stats (phi, psi) and cdl_dict_update (PGD + Armijo on D),
+issued as one cdl_step call (``--api calls``: the four calls one by one).
 Every step starts from the same X and initial D.  The metric is solves/s
 (one solve per step) with p50/p99 step latency and coordinate updates/s.
 
@@ -60,6 +61,8 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=32.0, help="served: HBM admission budget")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"],
                     help="served: beta-init precision of the served arm")
+    ap.add_argument("--api", default="step", choices=["step", "calls"],
+                    help="signal: one cdl_step call per step (default) or the four separate calls")
     ap.add_argument("--no-tune", action="store_true",
                     help="served: skip the sub-domain / stop-margin autotuner (library defaults)")
     return ap.parse_args()
@@ -145,10 +148,10 @@ class ClockSampler:
 class GpuStep:
     """Device-resident buffers and one hot-path step through the C ABI."""
 
-    def __init__(self, X, D0, w, device):
+    def __init__(self, X, D0, w, device, api="step"):
         import torch
         import paper_1901_09235_gb300 as pkg
-        self.pkg, self.w = pkg, w
+        self.pkg, self.w, self.api = pkg, w, api
         self.X = torch.from_numpy(X).to(device)
         self.D0 = torch.from_numpy(D0).to(device)
         self.D = self.D0.clone()
@@ -163,6 +166,13 @@ class GpuStep:
         if D is None:
             self.D.copy_(self.D0, non_blocking=True)
             D = self.D
+        if self.api == "step":
+            _, st = pkg.cdl_step(Xd, D, p, reg=self.w.reg, tol=self.w.tol, x_sqnorm=self.xs, pgd_max_iter=50,
+                                 pgd_tol=1e-8, opts=self.opts)
+            if st["status"] != pkg.CSC_OK:
+                raise RuntimeError(f"solve status {st['status']}: {pkg.status_string(st['status'])}")
+            self.last = st
+            return st
         _, _, lmax = pkg.csc_init_beta(Xd, D, p.beta, p.dtd, p.ws)
         lam = self.w.reg * lmax
         Z, st = pkg.csc_lgcd_solve(Xd, D, p.dtd, p.beta, lam, self.w.tol, Z=p.Z, opts=self.opts,
@@ -755,7 +765,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     X, D0, _ = make_problem(w, args.seed + rank)
-    step = GpuStep(X, D0, w, device)
+    step = GpuStep(X, D0, w, device, api=args.api)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
 
@@ -808,7 +818,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": config_dict(w, {"parallelism": f"replicas{world}" if world > 1 else "single",
-                                  "workers": last["workers"], "tile": last["tile_size"][0]}),
+                                  "workers": last["workers"], "tile": last["tile_size"][0],
+                                  "api": "cdl_step" if args.api == "step" else "four calls"}),
         "updates_per_s": world * upd / tot,
         "p50_ms": 1e3 * float(np.percentile(times, 50)),
         "p99_ms": 1e3 * float(np.percentile(times, 99)),

@@ -184,7 +184,9 @@ CSC_API int cdl_dict_stats(const csc_shape *shape, const float *Z, const float *
  * iteration starts from twice the last accepted step; at most max_iter
  * iterations, stop when ||D+ - D|| < tol ||D||.  D is held in FP32, so a
  * relative change below 4 x 2^-24 cannot be resolved: a smaller tol acts as
- * 4 x 2^-24.
+ * 4 x 2^-24.  The step also stops when its FP32 estimate of ||D+ - D||^2
+ * (from per-atom scalars) lies within its own rounding bound, where the
+ * change can no longer be resolved.
  *   D: in/out.  x_sqnorm: ||X||_2^2.  objective_out: host pointer (may be
  *   NULL) receiving F(D) = 1/2||X - Z*D||^2 at the end (FP64);
  *   iterations_out: host pointer (may be NULL).
@@ -213,6 +215,31 @@ CSC_API int cdl_fit(const csc_shape *shape, const float *X, float *D, float *Z, 
                     float *phi, float *psi, double reg, double tol, int max_outer, double nu,
                     int pgd_max_iter, double pgd_tol, const csc_solve_opts *opts, void *workspace,
                     size_t workspace_bytes, double *trace, int *n_outer, csc_stream_t stream);
+
+/* One pass of the loop body of Alg. 2 as a single call:
+ *   beta, dtd, lambda_max <- csc_init_beta(X, D);  lambda = reg * lambda_max
+ *   (of this D, rounded to float as csc_lgcd_solve receives it);
+ *   Z <- csc_lgcd_solve(X, D, lambda, tol, opts) (from Z = 0 unless
+ *        opts->warm_start);
+ *   phi, psi <- cdl_dict_stats(Z, X);
+ *   D <- cdl_dict_update(phi, psi, x_sqnorm) (pgd_max_iter, pgd_tol).
+ * Same buffers, layouts and results as those four calls; between the
+ * statistics and the dictionary step nothing waits for the device (the
+ * nonzero count is read back once, with the dictionary step's results).
+ *   D: in / out.  Z, beta, dtd, phi, psi: outputs.  x_sqnorm: ||X||_2^2.
+ *   stats: the solve's statistics (may be NULL).  lambda_out, dict_cost_out
+ *   (F(D) after the step, as cdl_dict_update's objective_out) and
+ *   dict_iters_out: host pointers (may be NULL).
+ * Synchronises `stream` three times (lambda_max, the end of the solve, the
+ * end of the step).  Returns the solve's status (CSC_OK or CSC_NOT_CONVERGED;
+ * the dictionary step still ran), CSC_ERR_WORKSPACE when Z has more nonzeros
+ * than the workspace's list holds (phi, psi and D are then not valid), or the
+ * first error of a stage. */
+CSC_API int cdl_step(const csc_shape *shape, const float *X, float *D, float *Z, float *beta, float *dtd,
+                     float *phi, float *psi, double reg, double tol, double x_sqnorm, int pgd_max_iter,
+                     double pgd_tol, const csc_solve_opts *opts, void *workspace, size_t workspace_bytes,
+                     csc_solve_stats *stats, double *lambda_out, double *dict_cost_out,
+                     int *dict_iters_out, csc_stream_t stream);
 
 /* csc_init_beta with the correlation on the tensor cores (tcgen05) in
  * split-bf16 precision: each X and D value is split into bf16 hi + lo parts

@@ -2,11 +2,14 @@
 // repeat { Z <- CSC(X, D) by LGCD with soft-locks; phi, psi <- statistics of
 // Z; D <- PGD with Armijo on (phi, psi) } until the cost varies by less than
 // nu (relative) or max_outer iterations are done.  Host-side driver over the
-// kernels of the other files; every step runs on the GPU.
+// kernels of the other files; every step runs on the GPU.  cdl_step is one
+// pass of the loop body as a single call.
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 
 #include "common.cuh"
+#include "dict.cuh"
 
 namespace csc {
 
@@ -97,4 +100,49 @@ extern "C" int cdl_fit(const csc_shape *shape, const float *X, float *D, float *
     }
     if (n_outer) *n_outer = q;
     return status;
+}
+
+extern "C" int cdl_step(const csc_shape *shape, const float *X, float *D, float *Z, float *beta, float *dtd,
+                        float *phi, float *psi, double reg, double tol, double x_sqnorm, int pgd_max_iter,
+                        double pgd_tol, const csc_solve_opts *opts, void *ws, size_t ws_bytes,
+                        csc_solve_stats *stats, double *lambda_out, double *dict_cost_out, int *dict_iters_out,
+                        csc_stream_t stream) {
+    Geom g;
+    int rc = make_geom(shape, &g);
+    if (rc) return rc;
+    if (!X || !D || !Z || !beta || !dtd || !phi || !psi || !ws) return CSC_ERR_INVALID;
+    if (!(reg > 0.0) || !(tol > 0.0) || !(x_sqnorm >= 0.0) || pgd_max_iter < 0 || !(pgd_tol >= 0.0))
+        return CSC_ERR_INVALID;
+    WsLayout L = plan_workspace(g, 0, 4);
+    if (ws_bytes < L.total) return CSC_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *wsb = static_cast<unsigned char *>(ws);
+    WsHeader *h = reinterpret_cast<WsHeader *>(wsb + L.hdr);
+
+    // beta, the D^T D table and lambda_max; lambda = reg * lambda_max of this D
+    double lmax = 0.0;
+    if ((rc = csc_init_beta(shape, X, D, beta, dtd, &lmax, ws, ws_bytes, stream))) return rc;
+    const float lambda = (float)(reg * lmax);
+    if (lambda_out) *lambda_out = lambda;
+    // Z by LGCD with soft-locks (Alg. 3)
+    const int solve_rc = csc_lgcd_solve(shape, X, D, dtd, beta, Z, lambda, (float)tol, opts, ws, ws_bytes,
+                                        stats, stream);
+    if (solve_rc != CSC_OK && solve_rc != CSC_NOT_CONVERGED) return solve_rc;
+    // phi, psi and the dictionary step, queued without a synchronisation in between
+    if ((rc = dict_stats_deferred(g, Z, X, phi, psi, wsb, L, st))) return rc;
+    if ((rc = dict_update_impl(g, phi, psi, x_sqnorm, D, pgd_max_iter, pgd_tol, nullptr, nullptr, wsb, L, st)))
+        return rc;
+    // one read-back: the dictionary step's results and the nonzero count
+    struct Tail {
+        double pgd[12];
+        int scan_total;
+    };
+    static_assert(offsetof(WsHeader, scan_total) == offsetof(WsHeader, pgd_out) + sizeof(double) * 12,
+                  "pgd_out and scan_total are adjacent");
+    Tail t;
+    if ((rc = read_back(&t, &h->pgd_out[0], st))) return rc;
+    if (t.scan_total > L.nnz_cap) return CSC_ERR_WORKSPACE;
+    if (dict_cost_out) *dict_cost_out = t.pgd[0];
+    if (dict_iters_out) *dict_iters_out = (int)t.pgd[1];
+    return solve_rc;
 }

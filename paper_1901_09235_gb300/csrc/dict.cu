@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dict.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -120,16 +121,16 @@ constexpr int kPsiChunk = 64;
 
 template <int NT>
 __global__ void __launch_bounds__(NT) psi_kernel(const int *nk, const int *ns, const float *nzv,
-                                                 const WsHeader *h, const float *X, double *psi64,
+                                                 const WsHeader *h, int cap, const float *X, double *psi64,
                                                  int P, int K, int T0, int T1, int L0, int L1, int Z1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *acc = reinterpret_cast<float *>(smem_raw);
     __shared__ int c_k[kPsiChunk], c_off[kPsiChunk];
     __shared__ float c_z[kPsiChunk];
     const int LL = L0 * L1, per = P * LL;
-    const int cnt = h->scan_total;
+    const int cnt = h->scan_total;  // a count above cap: the list was not written
     const int lo = blockIdx.x * kPsiChunk, n = min(cnt, lo + kPsiChunk) - lo;
-    if (n <= 0) return;
+    if (n <= 0 || cnt > cap) return;
     for (int q = threadIdx.x; q < K * per; q += NT) acc[q] = 0.f;
     for (int q = threadIdx.x; q < n; q += NT) {
         const int s = ns[lo + q], i = s / Z1;
@@ -167,9 +168,10 @@ __device__ __forceinline__ int lower_bound_pos(const int *ns, int n, int key) {
     return lo;
 }
 
-__global__ void phi_pairs_kernel(const int *nk, const int *ns, const float *nzv, const WsHeader *h,
+__global__ void phi_pairs_kernel(const int *nk, const int *ns, const float *nzv, const WsHeader *h, int cap,
                                  double *phi64, int K, int L0, int L1, int Z0, int Z1) {
     const int cnt = h->scan_total;
+    if (cnt > cap) return;  // the list was not written
     const int W0 = 2 * L0 - 1, W1 = 2 * L1 - 1;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < cnt; n += gridDim.x * blockDim.x) {
         const int k = nk[n], s = ns[n];
@@ -196,8 +198,12 @@ __global__ void to_float_kernel(const double *src, float *dst, long long n) {
         dst[i] = (float)src[i];
 }
 
-int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, float *psi,
-                    unsigned char *ws, const WsLayout &L, cudaStream_t st) {
+// count_on_host: read the nonzero count back (one synchronisation) to size the
+// phi / psi grids and report an overflow at once; otherwise the grids cover
+// the list capacity, the kernels read the count from the workspace header, and
+// the caller checks it against the capacity after a later synchronisation.
+static int stats_launch(const Geom &g, const float *Z, const float *X, float *phi, float *psi,
+                        unsigned char *ws, const WsLayout &L, cudaStream_t st, bool count_on_host) {
     WsHeader *h = reinterpret_cast<WsHeader *>(ws + L.hdr);
     int *nk = reinterpret_cast<int *>(ws + L.nnz_k);
     int *ns = reinterpret_cast<int *>(ws + L.nnz_s);
@@ -209,16 +215,19 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
     const long long zpos = g.nzpos();
     const int nblk = (int)ceil_div(zpos, 256);
     if (nblk > L.blk_cap) return CSC_ERR_WORKSPACE;
+    const int cap = (int)L.nnz_cap;
 
     nz_count_kernel<256><<<nblk, 256, 0, st>>>(Z, zpos, g.K, blk_cnt);
     nz_scan_kernel<1024><<<1, 1024, 0, st>>>(blk_cnt, blk_off, nblk, h);
-    int total = 0;
-    {
-        const int rb_ = read_back(&total, &h->scan_total, st);
+    long long total = cap;  // grid coverage
+    if (count_on_host) {
+        int t = 0;
+        const int rb_ = read_back(&t, &h->scan_total, st);
         if (rb_) return rb_;
+        if (t > cap) return CSC_ERR_WORKSPACE;
+        total = t;
     }
-    if (total > L.nnz_cap) return CSC_ERR_WORKSPACE;
-    nz_write_kernel<256><<<nblk, 256, 0, st>>>(Z, zpos, g.K, blk_off, h, L.nnz_cap, nk, ns, nzv);
+    nz_write_kernel<256><<<nblk, 256, 0, st>>>(Z, zpos, g.K, blk_off, h, cap, nk, ns, nzv);
     CSC_CUDA(cudaMemsetAsync(phi64, 0, (size_t)g.ntab() * sizeof(double), st));
     CSC_CUDA(cudaMemsetAsync(psi64, 0, (size_t)g.nd() * sizeof(double), st));
     if (total > 0) {
@@ -229,8 +238,8 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
             CSC_CUDA(cudaFuncSetAttribute(psi_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         psi_kernel<256><<<(int)ceil_div(total, chunk), 256, smem, st>>>(
-            nk, ns, nzv, h, X, psi64, g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z1);
-        phi_pairs_kernel<<<(int)ceil_div(total, 128), 128, 0, st>>>(nk, ns, nzv, h, phi64, g.K, g.L0,
+            nk, ns, nzv, h, cap, X, psi64, g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z1);
+        phi_pairs_kernel<<<(int)ceil_div(total, 128), 128, 0, st>>>(nk, ns, nzv, h, cap, phi64, g.K, g.L0,
                                                                     g.L1, g.Z0, g.Z1);
     }
     to_float_kernel<<<(int)std::min<long long>(ceil_div(g.ntab(), 256), 4096), 256, 0, st>>>(
@@ -239,6 +248,16 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
         psi64, psi, g.nd());
     CSC_CUDA(cudaGetLastError());
     return CSC_OK;
+}
+
+int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, float *psi,
+                    unsigned char *ws, const WsLayout &L, cudaStream_t st) {
+    return stats_launch(g, Z, X, phi, psi, ws, L, st, true);
+}
+
+int dict_stats_deferred(const Geom &g, const float *Z, const float *X, float *phi, float *psi,
+                        unsigned char *ws, const WsLayout &L, cudaStream_t st) {
+    return stats_launch(g, Z, X, phi, psi, ws, L, st, false);
 }
 
 // ====================================================== PGD + Armijo step

@@ -110,3 +110,36 @@ def test_cdl_image_8192_selfchecks(pkg, orc):
     assert abs(tr[-1][1] - f_ref) <= 1e-9 * abs(f_ref)
     nr = np.sqrt((host(Dd).reshape(w.K, -1).astype(np.float64) ** 2).sum(1))
     assert np.all(nr <= 1 + 1e-6)
+
+
+@pytest.mark.parametrize("w", [
+    Workload("step1d", P=5, K=10, T=(3001,), L=(64,), density=0.005, sigma=0.1),
+    Workload("step2d", P=2, K=5, T=(70, 150), L=(8, 12), density=0.01, sigma=0.1),
+], ids=["1d", "2d"])
+def test_cdl_step_matches_the_separate_calls(pkg, orc, w):
+    """cdl_step (one pass of the loop body in one call, the nonzero count read
+    back only at the end) gives what the four calls give: the same lambda, a
+    solve within 1e-5 of the oracle's objective, phi / psi equal to
+    cdl_dict_stats on its Z, and D, F and the iteration count of
+    cdl_dict_update on its phi / psi, bit for bit."""
+    import torch
+    X, D0, _ = make_problem(w, 43)
+    Xd = dev(X)
+    xs = float(np.sum(X.astype(np.float64) ** 2))
+    D = dev(D0)
+    prob = pkg.Problem.create(Xd, D)
+    Z, st = pkg.cdl_step(Xd, D, prob, reg=0.1, tol=1e-4, x_sqnorm=xs, pgd_max_iter=50, pgd_tol=1e-8)
+    assert st["status"] == 0
+    _, _, lm = pkg.csc_init_beta(Xd, dev(D0))
+    assert st["lambda"] == float(np.float32(0.1 * lm))
+    lam = st["lambda"]
+    f_ref = orc.objective(X, D0, orc.lgcd(X, D0, lam, 1e-4)["Z"], lam)
+    f_gpu = orc.objective(X, D0, host(Z).astype(np.float64), lam)
+    assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
+    phi2, psi2 = pkg.cdl_dict_stats(Z, Xd, tuple(D0.shape))
+    assert torch.allclose(prob.phi, phi2, rtol=1e-6, atol=0)
+    assert torch.allclose(prob.psi, psi2, rtol=1e-6, atol=0)
+    D2 = dev(D0)
+    F2, it2 = pkg.cdl_dict_update(prob.phi, prob.psi, xs, D2, tuple(X.shape), max_iter=50, tol=1e-8)
+    assert torch.equal(D2, D)
+    assert F2 == st["dict_F"] and it2 == st["dict_iters"]
