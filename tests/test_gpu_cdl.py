@@ -143,3 +143,25 @@ def test_cdl_step_matches_the_separate_calls(pkg, orc, w):
     F2, it2 = pkg.cdl_dict_update(prob.phi, prob.psi, xs, D2, tuple(X.shape), max_iter=50, tol=1e-8)
     assert torch.equal(D2, D)
     assert F2 == st["dict_F"] and it2 == st["dict_iters"]
+
+
+def test_cdl_step_reports_a_nonzero_list_overflow(pkg):
+    """A Z with more nonzeros than the workspace's list holds: cdl_step, which
+    reads the count back only at the end, still answers CSC_ERR_WORKSPACE
+    (the statistics kernels skip the unwritten list).  The dense Z comes from
+    a warm start that the solve leaves after one update (max_updates = 1)."""
+    import torch
+    w = Workload("dense1d", P=1, K=4, T=(400_000,), L=(16,), density=0.005, sigma=0.1)
+    X, D0, _ = make_problem(w, 47)
+    Xd, D = dev(X), dev(D0)
+    prob = pkg.Problem.create(Xd, D)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    prob.Z.copy_(0.01 * (torch.rand(prob.Z.shape, generator=gen, device="cuda") + 0.5))
+    opts = pkg.default_opts(warm_start=1, max_updates=1)
+    with pytest.raises(pkg.CscError) as e:
+        pkg.cdl_step(Xd, D, prob, reg=0.1, tol=1e-4, opts=opts)
+    assert e.value.status == pkg.CSC_ERR_WORKSPACE
+    # the separate statistics call reports the same overflow
+    with pytest.raises(pkg.CscError) as e2:
+        pkg.cdl_dict_stats(prob.Z, Xd, tuple(D0.shape), prob.phi, prob.psi, prob.ws)
+    assert e2.value.status == pkg.CSC_ERR_WORKSPACE
