@@ -128,6 +128,25 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
 
 
+def test_reference_arm_of_the_1d_workload_keeps_the_line_contract():
+    """The oracle arm of the headline workload prints one JSON line with the
+    keys the bench contract names (one bounded step, single process)."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+           "--warmup", "0"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["unit"] == "solves/s" and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "csc1d_T200000_P5_K10_L64" and line["steps"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"] > 0
+
+
 def test_autotune_classes_and_candidates():
     from paper_1901_09235_gb300 import autotune as at
     assert [at.size_class(s) for s in (64, 96, 97, 384, 385, 1536, 1537, 2048)] == [0, 0, 1, 2, 3, 4, 5, 5]
