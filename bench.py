@@ -1,23 +1,30 @@
 """Benchmark of the CSC hot path on GB300.
 
-One step = one pass of the whole path over one synthetic problem of the 1-D
-multichannel workload (P = 5, T = 200,000, K = 10 atoms of L = 64):
-  csc_init_beta (beta = D~ * X, the D^T D table, lambda_max)
-  csc_lgcd_solve (LGCD with soft-locks to max |dZ| < 1e-4, lambda = 0.1 lambda_max,
-                  FP64 objective and KKT on a beta recomputed from scratch)
-  cdl_dict_stats (phi, psi) and cdl_dict_update (PGD + Armijo on D),
-issued as one cdl_step call (``--api calls``: the four calls one by one).
-Every step starts from the same X and initial D.  The metric is solves/s
-(one solve per step) with p50/p99 step latency and coordinate updates/s.
+Default workload (``--workload image4096``): the plain large-image CSC solve,
+a 4096 x 4096 image (P = 1) with K = 25 atoms of 32 x 32, Z drawn
+Bernoulli(1e-4) x |N(0,1)|, noise sigma = 0.05, lambda = 0.1 lambda_max,
+tol 1e-4.  One step = one solve:
+  csc_init_beta  (beta = D~ * X, the D^T D table, lambda_max; FP32)
+  csc_lgcd_solve (LGCD over a 2-D grid of global-memory tiles with soft-locks
+                  to max |dZ| < tol, then beta recomputed from Z, the KKT test
+                  max |dZ| < tol on it and the FP64 objective)
+Every step starts from the same X and D.  The metric is solves/s with p50/p99
+step latency and coordinate updates/s.
+
+``--workload signal``: the 1-D multichannel workload (P = 5, T = 200,000,
+K = 10, L = 64), one step = csc_init_beta + csc_lgcd_solve + cdl_dict_stats +
+cdl_dict_update issued as one cdl_step call (``--api calls``: four calls).
+Other workloads (served trace, single served-family images, the coordinate
+selection and lambda sweeps) are listed under ``--workload``.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 launching stream; L2 is flushed (256 MiB write) between steps outside the
-events.  `e2e` repeats the measurement through host buffers (pinned X and D
-copied in, D and the objective copied out every step).
+events.  `e2e` repeats the measurement through host buffers (pinned inputs
+copied in, the step's result copied out, every step).
 
-``--impl reference`` times the FP64 CPU oracle on the same workload instead.
-Under torchrun (N > 1) every rank solves its own problem (independent
-replicas, no collective on the data path); value = all solves / max time.
+``--impl reference`` times the FP64 CPU oracle instead.  Under torchrun
+(N > 1) every rank solves its own problem (independent replicas, no
+collective on the data path); value = all solves / max time.
 """
 from __future__ import annotations
 
@@ -43,20 +50,25 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default 200 for the GPU arm of the 1-D workload, 20 otherwise)")
+                    help="timed steps (default 200 for the GPU arm of the 1-D workload, 30 for the "
+                         "4096^2 image, 20 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="signal", choices=["signal", "served", "image", "selection", "lambda"],
-                    help="signal: the 1-D multichannel solve + dictionary step (default); "
+    ap.add_argument("--workload", default="image4096",
+                    choices=["image4096", "signal", "served", "image", "selection", "lambda"],
+                    help="image4096: the plain 4096^2 CSC solve, 25 atoms of 32 x 32 (default); "
+                         "signal: the 1-D multichannel solve + dictionary step; "
                          "served: the request trace through the continuous-batching server; "
                          "image: single solves of one served-family image (--side); "
                          "selection: LGCD / greedy / randomized / cyclic CD on one worker (Section 5.1); "
                          "lambda: 2-D solves over lambda x workers x {greedy, LGCD}")
     ap.add_argument("--cap", type=float, default=60.0, help="selection / lambda: seconds per solve")
     ap.add_argument("--side", type=int, default=1024, help="image: side of the square image")
+    ap.add_argument("--crop", type=int, default=512,
+                    help="image4096: side of the crop of the same family that the oracle arms solve")
     ap.add_argument("--requests", type=int, default=512, help="served: requests in the trace")
     ap.add_argument("--rate", type=float, default=1000.0, help="served: Poisson arrival rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=32.0, help="served: HBM admission budget")
@@ -712,13 +724,255 @@ def lambda_main(args):
     return 0
 
 
+# ------------------------------------------------- the 4096^2 image (default)
+def large_image_workload():
+    from synthetic import IMAGE_4096
+    return IMAGE_4096
+
+
+def large_image_config(w, crop, extra=None):
+    d = {"workload": w.name, "P": w.P, "K": w.K, "T": list(w.T), "L": list(w.L), "density": w.density,
+         "activations": "|N(0,1)|" if w.nonneg else "N(0,1)", "sigma": w.sigma,
+         "lambda": f"{w.reg} * lambda_max", "tol": w.tol,
+         "step": "csc_init_beta (FP32) + csc_lgcd_solve (global-memory tiles, soft-locks; beta recomputed "
+                 "from Z, KKT max |dZ| < tol on it, FP64 objective)",
+         "l2": "flushed between steps (256 MiB write); beta and Z are 1.65 GB each, above L2",
+         "oracle_crop": f"{crop}x{crop} image of the same family (same generator, K, atoms, density, noise)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def image_algorithmic_bytes(st, w):
+    """Bytes one LGCD launch must move by its definition (same rule as the
+    1-D workload): 8 B per scanned candidate (beta, Z) over K x |C_m| per
+    iteration, 12 B per window entry (beta read + write, table) over K x |W|
+    plus 4 B of Z per accepted update."""
+    sub = int(np.prod([2 * l for l in w.L]))
+    win = int(np.prod([2 * l - 1 for l in w.L]))
+    return st["iterations"] * 8 * w.K * sub + st["updates"] * (12 * w.K * win + 4)
+
+
+def profile_value(name, key, sources):
+    """A value recorded in a committed ncu summary under profiles/, or None
+    when the kernel sources changed since it was taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", name)
+    src = [os.path.join(ROOT, "paper_1901_09235_gb300", "csrc", f) for f in sources]
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()
+    except OSError:
+        return None
+    vals = dict(line.split(" = ", 1) for line in text.splitlines() if " = " in line)
+    if vals.get("source_sha256", "").strip() != h or key not in vals:
+        return None
+    return float(vals[key])
+
+
+def crop_oracle_solve(w, crop, seed):
+    """One FP64 oracle solve of a crop-sized image of the same family: lambda_max,
+    LGCD to tol, objective.  Returns (seconds, updates, objective, lambda)."""
+    import oracle
+    from synthetic import make_problem, scaled
+    X, D, _ = make_problem(scaled(w, (crop, crop)), seed)
+    t0 = time.perf_counter()
+    lam = w.reg * oracle.lambda_max(X, D)
+    out = oracle.lgcd(X, D, lam, w.tol)
+    obj = oracle.objective(X, D, out["Z"], lam)
+    return time.perf_counter() - t0, out["n_updates"], obj, lam
+
+
+def large_image_main(args):
+    rank, world, local = dist_env()
+    w = large_image_workload()
+    crop = args.crop
+    area = (crop * crop) / float(w.T[0] * w.T[1])
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        oracle.build()
+        for i in range(args.warmup):
+            crop_oracle_solve(w, crop, args.seed + i)
+        times, upd = [], 0
+        for i in range(args.steps):
+            dt, u, _, _ = crop_oracle_solve(w, crop, args.seed + i)
+            times.append(dt)
+            upd += u
+        total = sum(times)
+        # whole-workload solves/s: a crop solve covers `area` of the image
+        val = area * args.steps / total
+        sample = (f"{args.steps} oracle solves of {crop}x{crop} crops of the same family (seeds "
+                  f"{args.seed}..{args.seed + args.steps - 1}), one core; solves/s of the {w.T[0]}x{w.T[1]} "
+                  f"image = crop solves/s x {area:.6g} (area ratio)")
+        line = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps / area,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": large_image_config(w, crop, {"arm": "FP64 CPU oracle, single thread, on crops"}),
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "updates_per_s": upd / total,
+                "crop_p50_ms": 1e3 * float(np.percentile(times, 50)),
+                "crop_p99_ms": 1e3 * float(np.percentile(times, 99))}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1901_09235_gb300 as pkg
+    from synthetic import make_dictionary, make_image_device
+    D = make_dictionary(np.random.default_rng(args.seed + 1000 * rank), w.K, w.P, w.L)
+    Dd = torch.from_numpy(D).to(device)
+    X = make_image_device(w, args.seed + 1000 * rank + 1, D, device)
+    s = pkg.make_shape(tuple(X.shape), tuple(Dd.shape))
+    opts = pkg.default_opts()
+    ws = pkg.workspace(s, opts, device=device)
+    beta = torch.empty(pkg.z_shape(s), dtype=torch.float32, device=device)
+    Z = torch.empty_like(beta)
+    dtd = torch.empty(pkg.tab_shape(s), dtype=torch.float32, device=device)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+
+    class Step:
+        def run(self, Xin=None, Din=None):
+            Xs, Ds = (X, Dd) if Xin is None else (Xin, Din)
+            _, _, lm = pkg.csc_init_beta(Xs, Ds, beta, dtd, ws)
+            _, st = pkg.csc_lgcd_solve(Xs, Ds, dtd, beta, w.reg * lm, w.tol, Z=Z, opts=opts, ws=ws)
+            if st["status"] != pkg.CSC_OK:
+                raise RuntimeError(f"solve status {st['status']}: {pkg.status_string(st['status'])}")
+            st["lambda"] = w.reg * lm
+            return st
+
+    step = Step()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clk = ClockSampler(local).__enter__()  # sampled over both timed loops below
+    times, stats = time_gpu(step, args.steps, max(3, args.warmup), flush, stream)
+    barrier()
+    # end to end: pinned X and D in, Z (dense FP32) and the objective out, every step
+    Xh = torch.empty(X.shape, dtype=torch.float32, pin_memory=True)
+    Xh.copy_(X)
+    Dh = torch.from_numpy(D).pin_memory()
+    Zh = torch.empty(Z.shape, dtype=torch.float32, pin_memory=True)
+    Xe, De = torch.empty_like(X), torch.empty_like(Dd)
+
+    def e2e_step():
+        Xe.copy_(Xh, non_blocking=True)
+        De.copy_(Dh, non_blocking=True)
+        st = step.run(Xe, De)  # the objective is copied to the host inside the call
+        Zh.copy_(Z, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return st
+
+    e2e_times, _ = time_gpu(step, args.steps, max(3, args.warmup), flush, stream, e2e=e2e_step)
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
+    barrier()
+    tot, tot_e2e = max_over_ranks([sum(times), sum(e2e_times)], device)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    upd = sum(st["updates"] for st in stats)
+    kernel_s = sum(st["kernel_ms"] for st in stats) / 1e3
+    abytes = sum(image_algorithmic_bytes(st, w) for st in stats)
+    achieved = abytes / kernel_s / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks["hbm_gbs"]) if "hbm_gbs" in peaks else 6800.0
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "6.8 TB/s (of fallback)"
+    traffic = profile_value("lgcd_global_kernel_csc2d_4096x4096_P1_K25_L32.md", "dram_bytes_per_launch",
+                            ("lgcd_global.cuh", "lgcd.cu", "lgcd_common.cuh", "common.cuh"))
+    last = stats[-1]
+    line = {
+        "metric": METRIC, "value": world * args.steps / tot, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": large_image_config(w, crop, {"parallelism": f"replicas{world}" if world > 1 else "single",
+                                               "workers": last["workers"], "tiles": last["tiles"],
+                                               "tile": last["tile_size"]}),
+        "updates_per_s": world * upd / tot,
+        "p50_ms": 1e3 * float(np.percentile(times, 50)),
+        "p99_ms": 1e3 * float(np.percentile(times, 99)),
+        "lgcd_kernel_ms_per_step": 1e3 * kernel_s / args.steps,
+        "lgcd_updates_per_s_kernel": upd / kernel_s,
+        "objective": last["objective"], "max_dz_final": last["max_dz_final"], "nnz": last["nnz"],
+        "updates_per_solve": upd / args.steps,
+        "solve_stats": {k: last[k] for k in ("iterations", "rejected_softlock", "skipped_subtol", "messages",
+                                              "refresh_rounds", "max_worker_iterations", "max_worker_updates",
+                                              "kernel_ms", "phase_cycles")},
+        "roofline": {"bound": "hbm", "kernel": "lgcd_global_kernel", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None if traffic is None else traffic,
+                     "peak_source": hbm_src, "algorithmic_bytes_per_launch": abytes / len(stats)},
+        "e2e": {"value": world * args.steps / tot_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(Xh.numel() * 4 + Dh.numel() * 4),
+                "d2h_bytes_per_step": int(Zh.numel() * 4 + 8)},
+        "gpu_launches": sum(launches_per_step_solve(st) for st in stats),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        # the oracle on crops of the same family, and the GPU on the same crop
+        import oracle
+        from synthetic import make_problem, scaled
+        oracle.build()
+        done, total, cu, obj0, lam0 = 0, 0.0, 0, None, None
+        while total < args.cpu_seconds and done < 10:
+            dt, u, obj, lam = crop_oracle_solve(w, crop, args.seed + done)
+            if done == 0:
+                obj0, lam0 = obj, lam
+            total += dt
+            cu += u
+            done += 1
+        line["cpu_baseline"] = {
+            "value": area * done / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} oracle solves of {crop}x{crop} crops of the same family, one core, "
+                      f"{total:.1f} s; solves/s of the full image = crop solves/s x {area:.6g} (area ratio)",
+            "updates_per_s": cu / total}
+        Xc, Dc, _ = make_problem(scaled(w, (crop, crop)), args.seed)
+        Xcd, Dcd = torch.from_numpy(Xc).to(device), torch.from_numpy(Dc).to(device)
+        bc, tc, _ = pkg.csc_init_beta(Xcd, Dcd)
+        _, stc = pkg.csc_lgcd_solve(Xcd, Dcd, tc, bc, lam0, w.tol)
+        line["crop_parity"] = {"side": crop, "objective_gpu": stc["objective"], "objective_oracle": obj0,
+                               "objective_rel_err_vs_oracle": abs(stc["objective"] - obj0) / abs(obj0),
+                               "max_dz_final": stc["max_dz_final"]}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def launches_per_step_solve(st):
+    # init_beta: corr + dtd; solve: atom norms + per round (ctl memset, header
+    # reset, LGCD, 7 refresh kernels)
+    return 2 + 1 + 9 * int(st["refresh_rounds"])
+
+
 def main():
     args = parse()
     if args.steps is None:
         # enough timed steps on the 1-D GPU arm (about 1 ms each) for several
         # clock samples and a meaningful p99; the oracle arm and the longer
         # workloads keep 20
-        args.steps = 200 if (args.workload == "signal" and args.impl == "gb300") else 20
+        args.steps = 20
+        if args.impl == "gb300":
+            args.steps = {"signal": 200, "image4096": 30}.get(args.workload, 20)
+    if args.workload == "image4096":
+        return large_image_main(args)
     if args.workload == "served":
         return served_main(args)
     if args.workload == "selection":

@@ -63,6 +63,7 @@ def _load():
             "orc_objective_sparse": (d, [i, i, i, i, i, i, p, p, p, d]),
             "orc_objective_nz": (d, [i, i, i, i, i, i, p, p, C.c_longlong, p, p, p, p, d]),
             "orc_rcd": (ll, [i, i, i, i, i, i, p, d, p, ll, p, p]),
+            "orc_phi_psi_nz": (i, [i, i, i, i, i, i, p, ll, p, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -305,6 +306,30 @@ def objective_nz(X, D, k, i, j, z, lam: float) -> float:
         raise ValueError("index and value arrays differ in length")
     return float(_load().orc_objective_nz(*_geom(X, D), _ptr(X), _ptr(D), len(z), _ptr(k), _ptr(i),
                                           _ptr(j), _ptr(z), float(lam)))
+
+
+def phi_psi_nz(X, L, K, k, i, j, z):
+    """phi and psi from the nonzeros of Z given as index arrays (k, i, j) and
+    values z (1-D problems: i all zeros, j the position), for activation maps
+    too large for the dense routine.  Shapes as ``phi_psi`` returns them."""
+    X = _f64(X)
+    d = X.ndim - 1
+    L0, L1 = (1, L[0]) if d == 1 else tuple(L)
+    P = X.shape[0]
+    T0, T1 = (1, X.shape[1]) if d == 1 else X.shape[1:]
+    k, i, j = (np.ascontiguousarray(np.asarray(v), dtype=np.int64) for v in (k, i, j))
+    z = _f64(np.asarray(z))
+    if not (len(k) == len(i) == len(j) == len(z)):
+        raise ValueError("index and value arrays differ in length")
+    phi = np.zeros((K, K, 2 * L0 - 1, 2 * L1 - 1))
+    psi = np.zeros((K, P, L0, L1))
+    rc = _load().orc_phi_psi_nz(P, K, T0, T1, L0, L1, _ptr(X), len(z), _ptr(k), _ptr(i), _ptr(j), _ptr(z),
+                                _ptr(phi), _ptr(psi))
+    if rc != 0:
+        raise ValueError("nonzero index outside the activation domain")
+    if d == 1:
+        return phi[:, :, 0, :].copy(), psi[:, :, 0, :].copy()
+    return phi, psi
 
 
 def cdl(X, D0, reg: float, tol: float, n_outer: int, pgd_max_iter: int = 50, pgd_tol: float = 1e-8):

@@ -661,3 +661,56 @@ double orc_objective_nz(int P, int K, int T0, int T1, int L0, int L1, const doub
     free(res);
     return 0.5 * f + lambda * g;
 }
+
+/* phi and psi (Eq. phi; psi = Z~ * X on Theta) from a list of nonzeros
+ * (atom k, row i, column j, value z) instead of a dense Z, for activation maps
+ * too large to hold on the host in FP64.  The list must not repeat a
+ * coordinate.  psi takes each nonzero's term directly; for phi the nonzeros
+ * are grouped by row (a counting sort), and every nonzero a is paired with
+ * every nonzero b whose row and column lie within L_i - 1 of its own, adding
+ * z_a z_b to phi_{k_a,k_b}[s_b - s_a]: exactly the nonzero terms of
+ * sum_s Z_k[s] Z_k2[s + d] for d in Phi.  Returns 0, or -1 for an index
+ * outside the activation domain. */
+int orc_phi_psi_nz(int P, int K, int T0, int T1, int L0, int L1, const double *X,
+                   long long nnz, const long long *kk, const long long *ii,
+                   const long long *jj, const double *zz, double *phi, double *psi)
+{
+    int Z0 = T0 - L0 + 1, Z1 = T1 - L1 + 1;
+    int W0 = 2 * L0 - 1, W1 = 2 * L1 - 1;
+    memset(phi, 0, (size_t)K * K * W0 * W1 * sizeof(double));
+    memset(psi, 0, (size_t)K * P * L0 * L1 * sizeof(double));
+    for (long long n = 0; n < nnz; n++)
+        if (kk[n] < 0 || kk[n] >= K || ii[n] < 0 || ii[n] >= Z0 || jj[n] < 0 || jj[n] >= Z1)
+            return -1;
+    /* psi_kp[tau] += z X_p[s + tau] */
+    for (long long n = 0; n < nnz; n++) {
+        int k = (int)kk[n], i = (int)ii[n], j = (int)jj[n];
+        for (int p = 0; p < P; p++)
+            for (int a = 0; a < L0; a++)
+                for (int b = 0; b < L1; b++)
+                    psi[IDX4(k, p, a, b, P, L0, L1)] += zz[n] * X[IDX3(p, i + a, j + b, T0, T1)];
+    }
+    /* nonzeros by row: start[r] .. start[r + 1] in `order` */
+    long long *start = calloc((size_t)Z0 + 1, sizeof(long long));
+    long long *fill = calloc((size_t)Z0, sizeof(long long));
+    long long *order = malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(long long));
+    for (long long n = 0; n < nnz; n++) start[ii[n] + 1]++;
+    for (int r = 0; r < Z0; r++) start[r + 1] += start[r];
+    for (long long n = 0; n < nnz; n++) order[start[ii[n]] + fill[ii[n]]++] = n;
+    for (long long a = 0; a < nnz; a++) {
+        int ka = (int)kk[a], ia = (int)ii[a], ja = (int)jj[a];
+        int r0 = ia - (L0 - 1) < 0 ? 0 : ia - (L0 - 1);
+        int r1 = ia + (L0 - 1) >= Z0 ? Z0 - 1 : ia + (L0 - 1);
+        for (int r = r0; r <= r1; r++)
+            for (long long q = start[r]; q < start[r + 1]; q++) {
+                long long b = order[q];
+                int d0 = r - ia, d1 = (int)jj[b] - ja;
+                if (d1 <= -L1 || d1 >= L1) continue;
+                phi[IDX4(ka, kk[b], d0 + L0 - 1, d1 + L1 - 1, K, W0, W1)] += zz[a] * zz[b];
+            }
+    }
+    free(start);
+    free(fill);
+    free(order);
+    return 0;
+}

@@ -30,3 +30,44 @@ def support_mismatch(z_a, z_b, tol, factor=100.0):
     diff = a ^ b
     vals = np.where(a & ~b, np.abs(z_a), np.where(b & ~a, np.abs(z_b), 0.0))
     return int(diff.sum()), float(vals.max()) if diff.any() else 0.0
+
+
+def kkt_fp64_within_bound(orc, X, D, Z, lam, tol, ks=None, ss=None):
+    """The KKT test of the oracle against the GPU's.
+
+    The GPU ends a solve only when max |dZ| < tol holds on a beta it
+    recomputes from Z in FP32: residual R = X - Z * D summed in FP64 and
+    rounded to FP32, beta_k[s] = sum over the n = P |Theta| taps of
+    D_kp[tau] R_p[s + tau] in FP32, plus ||D_k||^2 Z_k[s]; then
+    dZ = ST(beta, lambda) / ||D_k||^2 - Z.  Each of these FP32 values differs
+    from its FP64 counterpart by at most
+        |d beta| <= gamma_{n+3} (sum |D_kp[tau]| |R_p[s + tau]| + ||D_k||^2 |Z_k[s]|)
+    (one rounding of R, n - 1 sums, n products, two more operations), and
+    |d dZ| <= |d beta| / ||D_k||^2 + gamma_3 (|Z'| + |Z|) for the scaling and
+    the subtraction.  |R| <= |X| + |Z| * |D| is used for R.  So on the
+    oracle's FP64 beta every coordinate must satisfy
+        |dZ_64| < tol + |d dZ|,
+    which is what this returns (True / False) together with the largest
+    |dZ_64| and the largest bound, at the listed coordinates (k, row-major s)
+    or everywhere."""
+    X64, D64, Z64 = (np.asarray(a, dtype=np.float64) for a in (X, D, Z))
+    K = D64.shape[0]
+    n = int(np.prod(D64.shape[1:]))
+    nrm = orc.atom_sqnorms(D64)
+    Zf = Z64.reshape(K, -1)
+    if ks is None:
+        b64 = orc.beta_from_Z(X64, D64, Z64).reshape(K, -1)
+        # sum |D| (|X| + |Z| * |D|) = beta_from_Z(|X|, |D|, -|Z|) + ||D||^2 |Z|
+        babs = orc.beta_from_Z(np.abs(X64), np.abs(D64), -np.abs(Z64)).reshape(K, -1) + nrm[:, None] * np.abs(Zf)
+        nk = nrm[:, None]
+        z = Zf
+    else:
+        ks, ss = np.asarray(ks), np.asarray(ss)
+        b64 = orc.beta_from_Z_at(X64, D64, Z64, ks, ss)
+        babs = orc.beta_from_Z_at(np.abs(X64), np.abs(D64), -np.abs(Z64), ks, ss) + nrm[ks] * np.abs(Zf[ks, ss])
+        nk = nrm[ks]
+        z = Zf[ks, ss]
+    zn = np.sign(b64) * np.maximum(np.abs(b64) - lam, 0.0) / nk
+    dz = np.abs(zn - z)
+    bound = gamma(n + 3) * (babs + nk * np.abs(z)) / nk + gamma(3) * (np.abs(zn) + np.abs(z))
+    return bool(np.all(dz < tol + bound)), float(dz.max()), float(bound.max())

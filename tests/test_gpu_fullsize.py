@@ -3,15 +3,19 @@ configuration bench.py times (default options).
 
 * 1-D, P = 5, T = 200,000, K = 10, L = 64: the oracle finishes the whole
   problem in seconds, so everything is compared in full.
-* 2-D 4096 x 4096, K = 25 atoms of 32 x 32: too large for the full oracle;
-  outputs the oracle computes one by one (beta-init and beta recomputed from Z
-  at sampled coordinates, every nonzero of Z included) and properties that hold
-  at any size (objective from the nonzeros, KKT at the samples) are checked."""
+* 2-D 4096 x 4096, K = 25 atoms of 32 x 32: too large for the full oracle
+  solve; outputs the oracle computes one by one (beta-init and beta recomputed
+  from Z at sampled coordinates, every nonzero of Z included), properties that
+  hold at any size (objective from the nonzeros, KKT at the samples) and the
+  dictionary statistics phi / psi from the nonzeros of the GPU's Z are checked.
+* 2-D 1024 x 1024 image of the same family (same generator, 25 atoms of
+  32 x 32, density, noise): the full oracle solve, against the same
+  global-tile path."""
 import numpy as np
 import pytest
 
-from synthetic import IMAGE_4096, SIGNAL_200K, make_problem
-from tests._gpu import dev, gamma, host, support_mismatch
+from synthetic import IMAGE_4096, SIGNAL_200K, make_problem, scaled
+from tests._gpu import dev, gamma, host, kkt_fp64_within_bound, support_mismatch
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +49,9 @@ def test_signal_200k_full(pkg, orc):
     f_gpu = orc.objective(X, D, Zh, lam)
     assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
     assert abs(st["objective"] - f_gpu) <= 1e-6 * abs(f_gpu)
-    assert orc.kkt(X, D, Zh, lam) < 1.05 * w.tol
+    assert st["max_dz_final"] < w.tol
+    # FP64 KKT within the FP32 recomputation's rounding bound (tests/_gpu.py)
+    assert kkt_fp64_within_bound(orc, X, D, Zh, lam, w.tol)[0]
     cnt, worst = support_mismatch(Zh, ref["Z"], w.tol)
     assert cnt <= max(10, 0.01 * int((ref["Z"] != 0).sum())) and worst <= 100 * w.tol
     # dictionary statistics and step on the GPU solution
@@ -97,17 +103,50 @@ def test_image_4096_global_tiles(pkg, orc):
     # objective from the nonzeros (any size); lambda as the solver received it (fp32)
     f_ref = orc.objective_sparse(X, D, Zh, float(np.float32(lam)))
     assert abs(st["objective"] - f_ref) <= 1e-9 * abs(f_ref)
-    # KKT on beta recomputed from Z by the oracle, at every nonzero (up to 200)
-    # and at random coordinates
+    # KKT on beta recomputed from Z by the oracle, at nonzeros (up to 200) and
+    # at random coordinates, within the FP32 recomputation's rounding bound
     nzk, nzs = np.nonzero(Zh.reshape(w.K, -1))
     pick = rng.permutation(len(nzk))[:200]
     ks2 = np.concatenate([nzk[pick], rng.integers(0, w.K, 200)])
     ss2 = np.concatenate([nzs[pick], rng.integers(0, n, 200)])
-    b = orc.beta_from_Z_at(X, D, Zh, ks2, ss2)
-    nrm = orc.atom_sqnorms(D)[ks2]
-    zc = Zh.reshape(w.K, -1)[ks2, ss2].astype(np.float64)
-    dz = np.abs(np.sign(b) * np.maximum(np.abs(b) - lam, 0) / nrm - zc)
-    assert dz.max() < 1.05 * w.tol
-    # psi from the nonzeros against the oracle
+    ok, dzmax, bmax = kkt_fp64_within_bound(orc, X, D, Zh, float(np.float32(lam)), w.tol, ks2, ss2)
+    assert ok, (dzmax, bmax)
+    # phi and psi of the GPU's Z against the oracle's, from the nonzeros
     phi, psi = pkg.cdl_dict_stats(Z, Xd, D.shape, prob.phi, prob.psi, prob.ws)
-    assert np.isfinite(host(phi)).all()
+    zi, zj = nzs // Tz[1], nzs % Tz[1]
+    zv = Zh.reshape(w.K, -1)[nzk, nzs]
+    pr, sr = orc.phi_psi_nz(X, w.L, w.K, nzk, zi, zj, zv)
+    pa, sa = orc.phi_psi_nz(np.abs(X), w.L, w.K, nzk, zi, zj, np.abs(zv))
+    # phi: FP64 products and sums, rounded once to FP32
+    assert np.all(np.abs(host(phi) - pr) <= 2.0 ** -24 * np.abs(pr) + 1e-12 * pa)
+    # psi: FP32 sums over chunks of at most 64 nonzeros, FP64 across chunks,
+    # rounded once to FP32
+    assert np.all(np.abs(host(psi) - sr) <= gamma(65) * sa + 1e-12 * np.abs(sr).max())
+
+
+def test_image_1024_of_the_4096_family_against_the_oracle_solve(pkg, orc):
+    """The full oracle solve (Alg. 1, FP64) of a 1024 x 1024 image drawn like
+    the 4096 x 4096 workload, against the GPU's global-tile path with the
+    default options: objective within 1e-5 relative, support within the
+    stated count, KKT on the GPU and on the oracle's FP64 beta."""
+    w = scaled(IMAGE_4096, (1024, 1024))
+    X, D, _ = make_problem(w, 3)
+    lam = w.reg * orc.lambda_max(X, D)
+    ref = orc.lgcd(X, D, lam, w.tol)
+    assert ref["status"] == 0
+    Xd, Dd = dev(X), dev(D)
+    prob = pkg.Problem.create(Xd, Dd)
+    beta, dtd, _ = pkg.csc_init_beta(Xd, Dd, prob.beta, prob.dtd, prob.ws)
+    Z, st = pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, lam, w.tol, Z=prob.Z, ws=prob.ws)
+    assert st["status"] == 0 and st["placement"] == 2 and st["workers"] > 1, st
+    assert st["max_dz_final"] < w.tol
+    Zh = host(Z)
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    f_gpu = orc.objective(X, D, Zh, lam)
+    assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref), (f_gpu, f_ref)
+    assert abs(st["objective"] - f_gpu) <= 1e-6 * abs(f_gpu)
+    ok, dzmax, bmax = kkt_fp64_within_bound(orc, X, D, Zh, float(np.float32(lam)), w.tol)
+    assert ok, (dzmax, bmax)
+    nnz = int((ref["Z"] != 0).sum())
+    cnt, worst = support_mismatch(Zh, ref["Z"], w.tol)
+    assert cnt <= max(10, 0.01 * nnz) and worst <= 100 * w.tol, (cnt, nnz, worst)

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from synthetic import Workload, make_problem
-from tests._gpu import dev, gamma, host, support_mismatch
+from tests._gpu import dev, gamma, host, kkt_fp64_within_bound, support_mismatch
 
 pytestmark = pytest.mark.gpu
 
@@ -106,7 +106,8 @@ def test_phased_fp32_objective(pkg, orc, w, tile):
     f_ref = orc.objective(X, D, ref["Z"], lam)
     f_gpu = orc.objective(X, D, host(Z), lam)
     assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
-    assert orc.kkt(X, D, host(Z), lam) < 1.05 * tol
+    # FP64 KKT within the FP32 recomputation's rounding bound (tests/_gpu.py)
+    assert kkt_fp64_within_bound(orc, X, D, host(Z), lam, tol)[0]
 
 
 ASYNC = [
@@ -137,7 +138,8 @@ def test_async_softlock_matches_oracle(pkg, orc, w):
     f_gpu = orc.objective(X, D, Zh, lam)
     assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
     assert abs(st["objective"] - f_gpu) <= 1e-6 * abs(f_gpu)
-    assert orc.kkt(X, D, Zh, lam) < 1.05 * tol
+    # FP64 KKT within the FP32 recomputation's rounding bound (tests/_gpu.py)
+    assert kkt_fp64_within_bound(orc, X, D, Zh, lam, tol)[0]
     nnz = int((ref["Z"] != 0).sum())
     cnt, worst = support_mismatch(Zh, ref["Z"], tol)
     assert cnt <= max(10, 0.01 * nnz), (cnt, nnz)
@@ -247,7 +249,8 @@ def test_async_global_tiles_match_oracle(pkg, orc, w):
     f_ref = orc.objective(X, D, ref["Z"], lam)
     f_gpu = orc.objective(X, D, Zh, lam)
     assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
-    assert orc.kkt(X, D, Zh, lam) < 1.05 * tol
+    # FP64 KKT within the FP32 recomputation's rounding bound (tests/_gpu.py)
+    assert kkt_fp64_within_bound(orc, X, D, Zh, lam, tol)[0]
     cnt, worst = support_mismatch(Zh, ref["Z"], tol)
     assert cnt <= max(10, 0.01 * int((ref["Z"] != 0).sum()))
     assert worst <= 100 * tol

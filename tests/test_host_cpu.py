@@ -128,11 +128,9 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
 
 
-def test_reference_arm_of_the_1d_workload_keeps_the_line_contract():
-    """The oracle arm of the headline workload prints one JSON line with the
-    keys the bench contract names (one bounded step, single process)."""
+def _reference_line(*extra):
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-           "--warmup", "0"]
+           "--warmup", "0", *extra]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
@@ -142,9 +140,25 @@ def test_reference_arm_of_the_1d_workload_keeps_the_line_contract():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["impl"] == "reference" and line["unit"] == "solves/s" and line["higher_is_better"] is True
-    assert line["config"]["workload"] == "csc1d_T200000_P5_K10_L64" and line["steps"] == 1
+    assert line["steps"] == 1
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"] > 0
+    return line
+
+
+def test_reference_arm_of_the_default_workload_keeps_the_line_contract():
+    """The oracle arm of the default workload (the 4096^2 image, timed on
+    crops of the same family) prints one JSON line with the keys the bench
+    contract names, its value scaled to whole-image solves by the area ratio."""
+    line = _reference_line("--crop", "128")
+    assert line["config"]["workload"] == "csc2d_4096x4096_P1_K25_L32"
+    assert "128x128" in line["cpu_baseline"]["sample"]
+    assert abs(line["ms_per_step"] * line["value"] - 1e3) < 1e-6 * 1e3
+
+
+def test_reference_arm_of_the_1d_workload_keeps_the_line_contract():
+    line = _reference_line("--workload", "signal")
+    assert line["config"]["workload"] == "csc1d_T200000_P5_K10_L64"
 
 
 def test_autotune_classes_and_candidates():

@@ -418,6 +418,47 @@ def test_sampled_routines_match_explicit_model(orc, w):
     assert abs(orc.objective_nz(X, D, k, i, j, Z[nz], lam) - f) <= 1e-12 * f
 
 
+@pytest.mark.parametrize("w", [W1D, W2D], ids=["1d", "2d"])
+def test_phi_psi_from_nonzeros_match_correlations(orc, w):
+    """phi and psi from a list of nonzeros (the routine used on activation
+    maps too large for the dense one) equal the correlations of their
+    definitions (Eq. phi), computed here with scipy's correlate, and the dense
+    routine, whatever the order of the list."""
+    from scipy.signal import correlate
+    X, D, Z = _problem(w, 23)
+    Z = Z.astype(np.float64)
+    if not Z.any():
+        Z.reshape(-1)[::7] = 0.5
+    L = w.L
+    K, P = w.K, w.P
+    Zs = Z if Z.ndim == 3 else Z[:, None, :]
+    Xs = X if X.ndim == 3 else X[:, None, :]
+    L0, L1 = (1, L[0]) if len(L) == 1 else L
+    N0, N1 = Zs.shape[1:]
+    phi_ref = np.zeros((K, K, 2 * L0 - 1, 2 * L1 - 1))
+    for k in range(K):
+        for k2 in range(K):
+            c = correlate(Zs[k2], Zs[k], mode="full")  # c[lag + N - 1] = sum_s Z_k[s] Z_k2[s + lag]
+            phi_ref[k, k2] = c[N0 - 1 - (L0 - 1):N0 - 1 + L0, N1 - 1 - (L1 - 1):N1 - 1 + L1]
+    psi_ref = np.zeros((K, P, L0, L1))
+    for k in range(K):
+        for p in range(P):
+            psi_ref[k, p] = correlate(Xs[p], Zs[k], mode="valid")  # sum_s Z_k[s] X_p[s + tau]
+    nz = np.nonzero(Zs)
+    perm = np.random.default_rng(3).permutation(len(nz[0]))
+    k, i, j = (a[perm] for a in nz)
+    phi, psi = orc.phi_psi_nz(X, L, K, k, i, j, Zs[nz][perm])
+    if len(L) == 1:
+        phi_ref, psi_ref = phi_ref[:, :, 0, :], psi_ref[:, :, 0, :]
+    np.testing.assert_allclose(phi, phi_ref, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(psi, psi_ref, rtol=1e-12, atol=1e-12)
+    pd, sd = orc.phi_psi(Z, X, L)
+    np.testing.assert_allclose(phi, pd, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(psi, sd, rtol=1e-12, atol=1e-13)
+    with pytest.raises(ValueError):
+        orc.phi_psi_nz(X, L, K, [0], [0], [N1], [1.0])
+
+
 @pytest.mark.parametrize("d0", [0.4, 1.0])
 @pytest.mark.parametrize("dims", [1, 2], ids=["1d", "2d"])
 def test_cdl_loop_one_tap_closed_form(orc, dims, d0):
