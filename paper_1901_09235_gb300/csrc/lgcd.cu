@@ -398,6 +398,9 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
         rc = make_plan_global(g, o, 2ll * num_sms(), rs, &pl);
     }
     if (rc) return rc;
+    // the FP32 global-tile worker reads and reduces beta / Z in 16-byte groups
+    if (global && rs == 4 && ((reinterpret_cast<uintptr_t>(beta) | reinterpret_cast<uintptr_t>(Z)) & 15))
+        return CSC_ERR_INVALID;
     const int W = pl.G0 * pl.G1;
     WsLayout L = plan_workspace(g, W, rs);
     if (ws_bytes < L.total) return CSC_ERR_WORKSPACE;
@@ -495,6 +498,8 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     WsHeader hh;
     for (int round = 0;; round++) {
         CSC_CUDA(cudaMemsetAsync(wsb + L.mbox_ctl, 0, (size_t)W * kDirs * 32 * sizeof(int), st));
+        // later rounds resume from the Z of the previous one
+        a.z_zero = (round == 0 && !o.warm_start) ? 1 : 0;
         reset_header_kernel<<<1, 1, 0, st>>>(hdr, W);
         CSC_CUDA(cudaGetLastError());
         void *args[] = {&a};

@@ -24,6 +24,7 @@ struct LgcdArgs {
     int K, Z0, Z1, L0, L1, W0, W1;
     int G0, G1, t0, t1, sub0, sub1;
     int mode, guard_on, cap, Mmax;
+    int z_zero;  // Z is all zero when the launch starts (cold start)
     real lambda, eps;
     long long max_updates;
     unsigned long long timeout_ns;

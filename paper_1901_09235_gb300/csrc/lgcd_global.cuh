@@ -2,6 +2,9 @@
 // each worker of Alg. 3), shared by the single-solve kernel and the batched
 // queue kernel.
 #pragma once
+#include <cstdint>
+#include <type_traits>
+
 #include "lgcd_common.cuh"
 
 namespace csc {
@@ -49,6 +52,165 @@ __device__ __forceinline__ Cand<real> warp_argmax(const Cand<real> &c) {
     return r;
 }
 
+// One 16-byte reduction: four consecutive floats added at L2 as one request
+// (p 16-byte aligned).  Lanes with nothing to add pass 0.
+__device__ __forceinline__ void red_add_v4(float *p, float x, float y, float z, float w) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w)
+                 : "memory");
+}
+
+// Vector form of the scan and of the window update, for FP32 arrays whose
+// beta and Z start on 16-byte boundaries.  A row segment of the array is
+// covered by the aligned groups of four floats that meet it: with s the
+// segment's first flat index mod 4, group j starts at flat index
+// (first - s + 4 j), and lanes outside the segment are masked.  Tasks
+// (atom, row, group) are dealt to the threads in order, so a warp covers whole
+// rows with consecutive 16-byte accesses; (atom, row, group) of a thread's next
+// task follow from its current one by a fixed step (no division per task).
+struct TaskStep {
+    int k, r, j;      // current task
+    int dk, dr, dj;   // step of NT tasks
+    int R, NG;        // rows per atom, groups per row
+    __device__ __forceinline__ void init(int t, int nt, int R_, int NG_) {
+        R = R_;
+        NG = NG_;
+        const int per_k = R * NG;
+        k = t / per_k;
+        const int rem = t - k * per_k;
+        r = rem / NG;
+        j = rem - r * NG;
+        dk = nt / per_k;
+        const int srem = nt - dk * per_k;
+        dr = srem / NG;
+        dj = srem - dr * NG;
+    }
+    __device__ __forceinline__ void next() {
+        j += dj;
+        r += dr;
+        k += dk;
+        if (j >= NG) {
+            j -= NG;
+            r++;
+        }
+        if (r >= R) {
+            r -= R;
+            k++;
+        }
+    }
+};
+
+// Candidates of sub-domain rows [r0, r0 + bh) x columns [c0, c0 + bw) of the
+// tile at (or0, oc0): B tasks' loads are issued before any is evaluated.
+// With `zskip` the sub-domain holds no nonzero of Z and Z is not read.
+template <int NT, int B>
+__device__ __forceinline__ Cand<float> scan_v4(const LgcdArgs<float> &a, const float *snrm, const float *sinv,
+                                               int or0, int oc0, int r0, int c0, int bh, int bw, bool zskip) {
+    const int K = a.K;
+    const long long plane = (long long)a.Z0 * a.Z1, nall = (long long)K * plane;
+    const int NG = (bw + 6) >> 2;  // groups of 4 that can meet bw columns
+    const int total = K * bh * NG;
+    Cand<float> c{-1.f, 0xffffffffu, 0.f, 0.f};
+    TaskStep ts;
+    ts.init(threadIdx.x, NT, bh, NG);
+    for (int t = threadIdx.x; t < total; t += B * NT) {
+        float4 bv[B], zv[B];
+        int tk[B], tr[B], tl[B];  // atom, tile row, first tile column of the group
+#pragma unroll
+        for (int u = 0; u < B; u++) {
+            tk[u] = -1;
+            if (t + u * NT < total) {
+                const int li = r0 + ts.r;
+                const long long row = (long long)ts.k * plane + (long long)(or0 + li) * a.Z1 + oc0 + c0;
+                const int sft = (int)(row & 3);
+                const int off = 4 * ts.j - sft;  // sub-domain column of the group's first lane
+                if (off < bw) {
+                    tk[u] = ts.k;
+                    tr[u] = li;
+                    tl[u] = c0 + off;
+                    const long long gf = row + off;
+                    if (gf + 3 < nall) {
+                        bv[u] = __ldcg(reinterpret_cast<const float4 *>(a.beta + gf));
+                        zv[u] = zskip ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                      : __ldcg(reinterpret_cast<const float4 *>(a.Z + gf));
+                    } else {  // the array's last group: element by element
+                        float b4[4], z4[4];
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const bool in = off + e >= 0 && off + e < bw;
+                            b4[e] = in ? __ldcg(a.beta + gf + e) : 0.f;
+                            z4[e] = (in && !zskip) ? __ldcg(a.Z + gf + e) : 0.f;
+                        }
+                        bv[u] = make_float4(b4[0], b4[1], b4[2], b4[3]);
+                        zv[u] = make_float4(z4[0], z4[1], z4[2], z4[3]);
+                    }
+                }
+            }
+            ts.next();
+        }
+#pragma unroll
+        for (int u = 0; u < B; u++) {
+            if (tk[u] < 0) continue;
+            const int k = tk[u];
+            const float nk = snrm[k], ik = sinv[k];
+            const float b4[4] = {bv[u].x, bv[u].y, bv[u].z, bv[u].w};
+            const float z4[4] = {zv[u].x, zv[u].y, zv[u].z, zv[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int lj = tl[u] + e;
+                if (lj >= c0 && lj < c0 + bw) {
+                    const float zn = coord_update(b4[e], a.lambda, nk, ik);
+                    const float dz = zn - z4[e];
+                    Cand<float> x{dz < 0.f ? -dz : dz, (unsigned)((tr[u] * a.t1 + lj) * K + k), zn, dz};
+                    if (better(x, c)) c = x;
+                }
+            }
+        }
+    }
+    return c;
+}
+
+// beta_k[s] -= C[k][k0][s - s0] dz over V(s0) within the domain, except
+// (k0, s0) itself (Eq. beta_update), as 16-byte reductions.
+template <int NT>
+__device__ __forceinline__ void window_v4(const LgcdArgs<float> &a, int k0, int gi0, int gj0, float dz) {
+    const int K = a.K, W0 = a.W0, W1 = a.W1;
+    const long long plane = (long long)a.Z0 * a.Z1, nall = (long long)K * plane;
+    const int NG = (W1 + 6) >> 2, total = K * W0 * NG;
+    const int gjs = gj0 - (a.L1 - 1);  // domain column of window column 0
+    const bool col_edge = gjs < 0 || gj0 + a.L1 - 1 >= a.Z1;
+    TaskStep ts;
+    ts.init(threadIdx.x, NT, W0, NG);
+    for (int t = threadIdx.x; t < total; t += NT) {
+        const int k = ts.k, rw = ts.r, j = ts.j;
+        ts.next();
+        const int gi = gi0 + rw - (a.L0 - 1);
+        if (gi < 0 || gi >= a.Z0) continue;
+        const long long row = (long long)k * plane + (long long)gi * a.Z1 + gjs;  // flat index of window column 0
+        const int cw0 = 4 * j - (int)(row & 3);  // window column of the group's first lane
+        if (cw0 >= W1) continue;
+        const float *crow = a.dtd + ((size_t)(k * K + k0) * W0 + rw) * W1;
+        float v[4];
+        unsigned ok = 0;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int cw = cw0 + e, gj = gjs + cw;
+            const bool in = cw >= 0 && cw < W1 && (!col_edge || (gj >= 0 && gj < a.Z1)) &&
+                            !(k == k0 && rw == a.L0 - 1 && cw == a.L1 - 1);
+            v[e] = in ? -(__ldg(crow + cw) * dz) : 0.f;
+            ok |= (in ? 1u : 0u) << e;
+        }
+        if (!ok) continue;
+        const long long gf = row + cw0;
+        if (gf >= 0 && gf + 3 < nall) {
+            red_add_v4(a.beta + gf, v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (ok >> e & 1u) atomicAdd(a.beta + gf + e, v[e]);
+        }
+    }
+}
+
 // The worker of tile w (all NT threads of the CTA); smem_raw holds at least
 // 2 K elements.  Returns when the solve of `a` ends.
 //
@@ -83,6 +245,10 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
     __shared__ unsigned long long s_deadline;
     __shared__ real s_guard;
     __shared__ int s_seen, s_cnt[5];  // updates, iterations, rejected, below tol, messages
+    // nonzeros of Z per sub-domain (tiles of at most 64): counted from a cold
+    // start, never below the true count; a sub-domain at zero is scanned
+    // without reading Z
+    __shared__ int s_nz[64];
     // SM cycles of thread 0 per phase: scan, wait for the scan barrier,
     // soft-lock, window update, update barrier and flags, pause
     __shared__ unsigned long long s_ph[6], s_t;
@@ -107,6 +273,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
     // pauses once no sub-domain is dirty.  Larger tiles scan cyclically and
     // pause after M quiet iterations.
     const bool use_mask = M <= 64;
+    for (int q = threadIdx.x; q < 64; q += NT) s_nz[q] = a.z_zero ? 0 : (1 << 24);
     unsigned long long dmask = 0, ring = 0;
     if (use_mask) {
         dmask = M == 64 ? ~0ull : ((1ull << M) - 1ull);
@@ -132,7 +299,11 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         const int r0 = mr * a.sub0, c0 = mc * a.sub1;
         const int bh = min(a.sub0, h - r0), bw = min(a.sub1, wd - c0);
         Cand<real> c{real(-1), 0xffffffffu, real(0), real(0)};
-        {
+        if constexpr (std::is_same<real, float>::value) {
+            // FP32: the vector scan (beta and Z start on 16-byte boundaries,
+            // checked by the host)
+            c = scan_v4<NT, RB / 3>(a, snrm, sinv, or0, oc0, r0, c0, bh, bw, use_mask && s_nz[m] == 0);
+        } else {
             const int nrb = (bh + kRowBlock - 1) / kRowBlock, nch = (bw + 31) >> 5, per_k = nrb * nch;
             for (int u = warp; u < K * per_k; u += NW) {
                 const int k = u / per_k, rem = u - k * per_k, rb = rem / nch, ch = rem - rb * nch;
@@ -313,30 +484,43 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                 accepted = true;
                 // Z first: the barrier after the window update publishes both
                 // to the next scan
-                if (threadIdx.x == 0) a.Z[k0 * plane + (size_t)gi0 * a.Z1 + gj0] = best.znew;
-                // beta_k[s] -= C[k][k0][s - s0] dz on V(s0) within the domain:
-                // the table loads of a unit first, then its reductions
+                if (threadIdx.x == 0) {
+                    a.Z[k0 * plane + (size_t)gi0 * a.Z1 + gj0] = best.znew;
+                    if (use_mask) {
+                        // Z was zero exactly when Z' - dZ is (dZ = Z' - 0 is exact);
+                        // the converse can fail only towards a larger count
+                        const bool was0 = best.znew - best.dz == real(0), now0 = best.znew == real(0);
+                        if (was0 && !now0) s_nz[m]++;
+                        else if (!was0 && now0) s_nz[m]--;
+                    }
+                }
+                // beta_k[s] -= C[k][k0][s - s0] dz on V(s0) within the domain
                 const real dz = best.dz;
-                const int W0 = a.W0, W1 = a.W1;
-                const int nrb = (W0 + kRowBlock - 1) / kRowBlock, nch = (W1 + 31) >> 5, per_k = nrb * nch;
-                for (int u = warp; u < K * per_k; u += NW) {
-                    const int k = u / per_k, rem = u - k * per_k, rb = rem / nch, ch = rem - rb * nch;
-                    const int cw = ch * 32 + lane, rw0 = rb * kRowBlock;
-                    const int gj = gj0 + cw - (a.L1 - 1), gi = gi0 + rw0 - (a.L0 - 1);
-                    // rows of this unit inside the domain: [q_lo, q_hi)
-                    const bool colok = cw < W1 && gj >= 0 && gj < a.Z1;
-                    const int q_lo = max(0, -gi), q_hi = colok ? min(min(kRowBlock, W0 - rw0), a.Z0 - gi) : 0;
-                    const real *crow = a.dtd + (((size_t)k * K + k0) * W0 + rw0) * W1 + cw;
-                    real cv[kRowBlock];
+                if constexpr (std::is_same<real, float>::value) {
+                    window_v4<NT>(a, k0, gi0, gj0, dz);
+                } else {
+                    // the table loads of a unit first, then its reductions
+                    const int W0 = a.W0, W1 = a.W1;
+                    const int nrb = (W0 + kRowBlock - 1) / kRowBlock, nch = (W1 + 31) >> 5, per_k = nrb * nch;
+                    for (int u = warp; u < K * per_k; u += NW) {
+                        const int k = u / per_k, rem = u - k * per_k, rb = rem / nch, ch = rem - rb * nch;
+                        const int cw = ch * 32 + lane, rw0 = rb * kRowBlock;
+                        const int gj = gj0 + cw - (a.L1 - 1), gi = gi0 + rw0 - (a.L0 - 1);
+                        // rows of this unit inside the domain: [q_lo, q_hi)
+                        const bool colok = cw < W1 && gj >= 0 && gj < a.Z1;
+                        const int q_lo = max(0, -gi), q_hi = colok ? min(min(kRowBlock, W0 - rw0), a.Z0 - gi) : 0;
+                        const real *crow = a.dtd + (((size_t)k * K + k0) * W0 + rw0) * W1 + cw;
+                        real cv[kRowBlock];
 #pragma unroll
-                    for (int q = 0; q < kRowBlock; q++)
-                        if (q >= q_lo && q < q_hi) cv[q] = __ldg(crow + q * W1);
-                    real *bk = a.beta + (size_t)k * plane;
-                    const int o0 = gi * a.Z1 + gj;
+                        for (int q = 0; q < kRowBlock; q++)
+                            if (q >= q_lo && q < q_hi) cv[q] = __ldg(crow + q * W1);
+                        real *bk = a.beta + (size_t)k * plane;
+                        const int o0 = gi * a.Z1 + gj;
 #pragma unroll
-                    for (int q = 0; q < kRowBlock; q++)
-                        if (q >= q_lo && q < q_hi && !(k == k0 && gi + q == gi0 && gj == gj0))
-                            atomicAdd(bk + (o0 + q * a.Z1), -(cv[q] * dz));
+                        for (int q = 0; q < kRowBlock; q++)
+                            if (q >= q_lo && q < q_hi && !(k == k0 && gi + q == gi0 && gj == gj0))
+                                atomicAdd(bk + (o0 + q * a.Z1), -(cv[q] * dz));
+                    }
                 }
                 if (threadIdx.x == 0) {
                     const unsigned long long t = clock64();

@@ -347,6 +347,7 @@ int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, c
 int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float lambda, float tol, int warm_start,
                      const csc_solve_opts *opts, int *job_out) {
     if (!q || !beta || !Z || !job_out || !(lambda >= 0.f) || !(tol > 0.f)) return CSC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(beta) | reinterpret_cast<uintptr_t>(Z)) & 15) return CSC_ERR_INVALID;
     const csc_solve_opts o = opts ? *opts : q->opts;
     if (!(o.stop_margin >= 0.0 && o.stop_margin <= 1.0) || o.mode < 0 || o.mode > 2) return CSC_ERR_INVALID;
     if (q->njobs >= q->max_jobs || q->free_ctl.empty()) return CSC_ERR_WORKSPACE;
@@ -399,6 +400,7 @@ int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float 
     a.guard_on = o.divergence_guard;
     a.cap = kMailboxCap;
     a.Mmax = 0;
+    a.z_zero = warm_start ? 0 : 1;
     a.lambda = lambda;
     a.eps = (float)(o.stop_margin > 0.0 ? o.stop_margin : 0.99) * tol;  // as in the single solve
     a.max_updates = 0;

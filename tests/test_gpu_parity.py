@@ -254,3 +254,19 @@ def test_async_global_tiles_match_oracle(pkg, orc, w):
     cnt, worst = support_mismatch(Zh, ref["Z"], tol)
     assert cnt <= max(10, 0.01 * int((ref["Z"] != 0).sum()))
     assert worst <= 100 * tol
+
+
+def test_global_tiles_refuse_beta_or_z_off_a_16_byte_boundary(pkg, orc):
+    """The FP32 global-tile worker reads and reduces beta and Z in aligned
+    groups of four: arrays that do not start on a 16-byte boundary are refused
+    on the host before any launch."""
+    import torch
+    w = ASYNC[3]
+    X, D, _ = make_problem(w, 36)
+    Xd, Dd = dev(X), dev(D)
+    beta, dtd, lm = pkg.csc_init_beta(Xd, Dd)
+    buf = torch.zeros(beta.numel() + 1, dtype=torch.float32, device=beta.device)
+    Zoff = buf[1:].view(beta.shape)
+    with pytest.raises(pkg.CscError) as e:
+        pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, 0.1 * lm, 1e-4, Z=Zoff, opts=pkg.default_opts(placement=2))
+    assert e.value.status == pkg.CSC_ERR_INVALID
