@@ -87,6 +87,11 @@ WsLayout plan_workspace(const Geom &g, int max_workers, int rs) {
     L.mbox_slots = take((size_t)max_workers * kDirs * kMailboxCap * sizeof(int4));
     L.mbox_ctl = take((size_t)max_workers * kDirs * 32 * sizeof(int));
     L.total = off;
+    // optional, after the required regions: the initial beta of an FP32
+    // solve, from which the global-tile solve rebuilds beta for its final
+    // KKT test (a workspace that ends at `total` takes the correlation)
+    L.beta0 = off;
+    L.total_beta0 = rs == 4 ? align256(off + (size_t)g.nz() * rs) : off;
     return L;
 }
 
@@ -157,7 +162,7 @@ int csc_workspace_size(const csc_shape *shape, const csc_solve_opts *opts, size_
     if (rc) return rc;
     if (!bytes) return CSC_ERR_INVALID;
     int w = worker_bound(g, opts);
-    size_t a = plan_workspace(g, w, 4).total, b = plan_workspace(g, w, 8).total;
+    size_t a = plan_workspace(g, w, 4).total_beta0, b = plan_workspace(g, w, 8).total;
     *bytes = std::max(a, b);
     return CSC_OK;
 }

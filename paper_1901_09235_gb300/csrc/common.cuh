@@ -72,7 +72,7 @@ constexpr int kDirs = 8;            // neighbour directions in a 2-D tile grid
 
 struct WsLayout {
     size_t hdr, nrm, dmax, nnz_k, nnz_s, nnz_z, blk, r64, rr, phi64, psi64, pgd, mbox_slots,
-        mbox_ctl, total;
+        mbox_ctl, total, beta0, total_beta0;  // beta0: optional region up to total_beta0
     long long nnz_cap;
     int max_workers;
     int blk_cap;
@@ -221,7 +221,7 @@ int launch_corr_init(const Geom &g, const real *X, const real *D, real *beta,
 template <typename real>
 int launch_corr_refresh(const Geom &g, const real *R, const real *D, const real *Z,
                         const double *nrm, real lambda, real *beta,
-                        unsigned long long *maxdz_bits, cudaStream_t st);
+                        unsigned long long *maxdz_bits, cudaStream_t st, const int *gate = nullptr);
 template <typename real>
 int launch_dtd(const Geom &g, const real *D, real *dtd, cudaStream_t st);
 
@@ -263,10 +263,13 @@ int launch_atom_norms(const Geom &g, const real *D, double *nrm, double *dmax, c
 
 // Residual / objective / KKT on the current Z (writes beta recomputed from
 // scratch when `beta` is non-null).  Leaves obj_f, obj_g, maxdz_bits, nnz in
-// the header.
+// the header.  With `dtd` given (FP32 only), beta is rebuilt from the initial
+// beta kept in the workspace's beta0 region: beta0 minus C * Z over the
+// nonzero list (the correlation of the residual when the list overflowed).
 template <typename real>
 int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const real *X,
-                   const real *D, const real *Z, real lambda, real *beta, cudaStream_t st);
+                   const real *D, const real *Z, real lambda, real *beta, cudaStream_t st,
+                   const real *dtd = nullptr);
 
 template <typename real>
 int solve_impl(const csc_shape *shape, const real *X, const real *D, const real *dtd, real *beta,

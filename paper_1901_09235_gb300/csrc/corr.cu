@@ -21,6 +21,7 @@ struct CorrArgs {
     real lambda;
     unsigned long long *bits;  // init: max |beta|; refresh: max |dZ|
     int P, K, T0, T1, L0, L1, Z0, Z1;
+    const int *gate;  // refresh: when set, the kernel runs only if *gate != 0
 };
 
 enum { EPI_INIT = 0, EPI_REFRESH = 1 };
@@ -32,6 +33,7 @@ enum { EPI_INIT = 0, EPI_REFRESH = 1 };
 // while the atom weight is a broadcast.
 template <typename real, int NT, int TR, int NQ, int KC, int EPI>
 __global__ void __launch_bounds__(NT) corr_kernel(CorrArgs<real> a) {
+    if (EPI == EPI_REFRESH && a.gate && *a.gate == 0) return;
     constexpr int TPR = NT / TR;
     constexpr int TC = TPR * NQ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(NT) corr_kernel(CorrArgs<real> a) {
 // channel by channel, tap row by tap row and tap by tap, as corr_kernel does.
 template <int NT, int TR, int NQ, int KC, int EPI>
 __global__ void __launch_bounds__(NT) corr_rows_kernel(CorrArgs<float> a) {
+    if (EPI == EPI_REFRESH && a.gate && *a.gate == 0) return;
     constexpr int TPR = NT / TR, TC = TPR * NQ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L0 = a.L0, L1 = a.L1, Lp = (L1 + NQ - 1) / NQ * NQ;
@@ -277,16 +280,16 @@ template <typename real>
 int launch_corr_init(const Geom &g, const real *X, const real *D, real *beta,
                      unsigned long long *lmax_bits, cudaStream_t st) {
     CorrArgs<real> a{X, D, beta, nullptr, nullptr, real(0), lmax_bits,
-                     g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z0, g.Z1};
+                     g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z0, g.Z1, nullptr};
     return corr_dispatch<real, EPI_INIT>(g, a, st);
 }
 
 template <typename real>
 int launch_corr_refresh(const Geom &g, const real *R, const real *D, const real *Z,
                         const double *nrm, real lambda, real *beta,
-                        unsigned long long *maxdz_bits, cudaStream_t st) {
+                        unsigned long long *maxdz_bits, cudaStream_t st, const int *gate) {
     CorrArgs<real> a{R, D, beta, Z, nrm, lambda, maxdz_bits,
-                     g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z0, g.Z1};
+                     g.P, g.K, g.T0, g.T1, g.L0, g.L1, g.Z0, g.Z1, gate};
     return corr_dispatch<real, EPI_REFRESH>(g, a, st);
 }
 
@@ -412,7 +415,7 @@ int preload_corr_kernels() {
                                         unsigned long long *, cudaStream_t);                  \
     template int launch_corr_refresh<real>(const Geom &, const real *, const real *,          \
                                            const real *, const double *, real, real *,        \
-                                           unsigned long long *, cudaStream_t);               \
+                                           unsigned long long *, cudaStream_t, const int *);  \
     template int launch_dtd<real>(const Geom &, const real *, real *, cudaStream_t);          \
     template int launch_atom_norms<real>(const Geom &, const real *, double *, double *,      \
                                          cudaStream_t);

@@ -433,6 +433,11 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     }
 
     if (!o.warm_start) CSC_CUDA(cudaMemsetAsync(Z, 0, (size_t)g.nz() * rs, st));
+    // FP32 global tiles from a cold start keep the initial beta: the final
+    // KKT test then rebuilds beta as beta0 - C * Z over the nonzeros of Z
+    // instead of correlating the residual again
+    const bool use_beta0 = global && rs == 4 && !o.warm_start && ws_bytes >= L.total_beta0;
+    if (use_beta0) CSC_CUDA(cudaMemcpyAsync(wsb + L.beta0, beta, (size_t)g.nz() * rs, cudaMemcpyDeviceToDevice, st));
     rc = launch_atom_norms<real>(g, D, nrm, dmax, st);
     if (rc) return rc;
 
@@ -507,7 +512,7 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
         CSC_CUDA(cudaLaunchCooperativeKernel(kern, dim3(W), dim3(kernel_threads(o.mode, global)), args, pl.smem, st));
         CSC_CUDA(cudaEventRecord(e1, st));
         // beta from scratch, KKT and objective on the current Z, then one sync
-        rc = launch_refresh<real>(g, L, wsb, X, D, Z, lambda, beta, st);
+        rc = launch_refresh<real>(g, L, wsb, X, D, Z, lambda, beta, st, use_beta0 ? dtd : nullptr);
         if (rc) return rc;
         S.refresh_rounds++;
         {

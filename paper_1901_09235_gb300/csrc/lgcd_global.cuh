@@ -53,10 +53,11 @@ __device__ __forceinline__ Cand<real> warp_argmax(const Cand<real> &c) {
 }
 
 // One 16-byte reduction: four consecutive floats added at L2 as one request
-// (p 16-byte aligned).  Lanes with nothing to add pass 0.
+// (p 16-byte aligned).  Lanes with nothing to add pass 0.  No memory clobber:
+// the only other accesses near it are read-only table loads, which may move
+// across it.
 __device__ __forceinline__ void red_add_v4(float *p, float x, float y, float z, float w) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w)
-                 : "memory");
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w));
 }
 
 // Vector form of the scan and of the window update, for FP32 arrays whose
@@ -100,34 +101,32 @@ struct TaskStep {
 };
 
 // Candidates of sub-domain rows [r0, r0 + bh) x columns [c0, c0 + bw) of the
-// tile at (or0, oc0): B tasks' loads are issued before any is evaluated.
+// tile at (or0, oc0): the loads of B tasks are issued before any is
+// evaluated; the evaluation replays the tasks' indices from a saved step.
 // With `zskip` the sub-domain holds no nonzero of Z and Z is not read.
 template <int NT, int B>
 __device__ __forceinline__ Cand<float> scan_v4(const LgcdArgs<float> &a, const float *snrm, const float *sinv,
                                                int or0, int oc0, int r0, int c0, int bh, int bw, bool zskip) {
     const int K = a.K;
     const long long plane = (long long)a.Z0 * a.Z1, nall = (long long)K * plane;
+    // low two bits of a flat index, from 32-bit arithmetic (they depend only
+    // on the low bits of each term)
+    const unsigned plane_lo = (unsigned)plane, base_lo = (unsigned)(or0 + r0) * (unsigned)a.Z1 + oc0 + c0;
     const int NG = (bw + 6) >> 2;  // groups of 4 that can meet bw columns
     const int total = K * bh * NG;
     Cand<float> c{-1.f, 0xffffffffu, 0.f, 0.f};
     TaskStep ts;
     ts.init(threadIdx.x, NT, bh, NG);
     for (int t = threadIdx.x; t < total; t += B * NT) {
+        const int k_s = ts.k, r_s = ts.r, j_s = ts.j;
         float4 bv[B], zv[B];
-        int tk[B], tr[B], tl[B];  // atom, tile row, first tile column of the group
 #pragma unroll
         for (int u = 0; u < B; u++) {
-            tk[u] = -1;
             if (t + u * NT < total) {
-                const int li = r0 + ts.r;
-                const long long row = (long long)ts.k * plane + (long long)(or0 + li) * a.Z1 + oc0 + c0;
-                const int sft = (int)(row & 3);
+                const int sft = (int)((ts.k * plane_lo + base_lo + (unsigned)ts.r * (unsigned)a.Z1) & 3u);
                 const int off = 4 * ts.j - sft;  // sub-domain column of the group's first lane
                 if (off < bw) {
-                    tk[u] = ts.k;
-                    tr[u] = li;
-                    tl[u] = c0 + off;
-                    const long long gf = row + off;
+                    const long long gf = (long long)ts.k * plane + (long long)(or0 + r0 + ts.r) * a.Z1 + oc0 + c0 + off;
                     if (gf + 3 < nall) {
                         bv[u] = __ldcg(reinterpret_cast<const float4 *>(a.beta + gf));
                         zv[u] = zskip ? make_float4(0.f, 0.f, 0.f, 0.f)
@@ -147,20 +146,27 @@ __device__ __forceinline__ Cand<float> scan_v4(const LgcdArgs<float> &a, const f
             }
             ts.next();
         }
+        TaskStep rs = ts;
+        rs.k = k_s;
+        rs.r = r_s;
+        rs.j = j_s;
 #pragma unroll
         for (int u = 0; u < B; u++) {
-            if (tk[u] < 0) continue;
-            const int k = tk[u];
+            const int k = rs.k, li = r0 + rs.r;
+            const int sft = (int)((k * plane_lo + base_lo + (unsigned)rs.r * (unsigned)a.Z1) & 3u);
+            const int lj0 = c0 + 4 * rs.j - sft;  // tile column of the group's first lane
+            rs.next();
+            if (t + u * NT >= total || lj0 >= c0 + bw) continue;
             const float nk = snrm[k], ik = sinv[k];
             const float b4[4] = {bv[u].x, bv[u].y, bv[u].z, bv[u].w};
             const float z4[4] = {zv[u].x, zv[u].y, zv[u].z, zv[u].w};
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                const int lj = tl[u] + e;
+                const int lj = lj0 + e;
                 if (lj >= c0 && lj < c0 + bw) {
                     const float zn = coord_update(b4[e], a.lambda, nk, ik);
                     const float dz = zn - z4[e];
-                    Cand<float> x{dz < 0.f ? -dz : dz, (unsigned)((tr[u] * a.t1 + lj) * K + k), zn, dz};
+                    Cand<float> x{dz < 0.f ? -dz : dz, (unsigned)((li * a.t1 + lj) * K + k), zn, dz};
                     if (better(x, c)) c = x;
                 }
             }
@@ -170,8 +176,9 @@ __device__ __forceinline__ Cand<float> scan_v4(const LgcdArgs<float> &a, const f
 }
 
 // beta_k[s] -= C[k][k0][s - s0] dz over V(s0) within the domain, except
-// (k0, s0) itself (Eq. beta_update), as 16-byte reductions.
-template <int NT>
+// (k0, s0) itself (Eq. beta_update), as 16-byte reductions.  The table loads
+// of B tasks are issued before their reductions.
+template <int NT, int B>
 __device__ __forceinline__ void window_v4(const LgcdArgs<float> &a, int k0, int gi0, int gj0, float dz) {
     const int K = a.K, W0 = a.W0, W1 = a.W1;
     const long long plane = (long long)a.Z0 * a.Z1, nall = (long long)K * plane;
@@ -180,33 +187,45 @@ __device__ __forceinline__ void window_v4(const LgcdArgs<float> &a, int k0, int 
     const bool col_edge = gjs < 0 || gj0 + a.L1 - 1 >= a.Z1;
     TaskStep ts;
     ts.init(threadIdx.x, NT, W0, NG);
-    for (int t = threadIdx.x; t < total; t += NT) {
-        const int k = ts.k, rw = ts.r, j = ts.j;
-        ts.next();
-        const int gi = gi0 + rw - (a.L0 - 1);
-        if (gi < 0 || gi >= a.Z0) continue;
-        const long long row = (long long)k * plane + (long long)gi * a.Z1 + gjs;  // flat index of window column 0
-        const int cw0 = 4 * j - (int)(row & 3);  // window column of the group's first lane
-        if (cw0 >= W1) continue;
-        const float *crow = a.dtd + ((size_t)(k * K + k0) * W0 + rw) * W1;
-        float v[4];
-        unsigned ok = 0;
+    for (int t = threadIdx.x; t < total; t += B * NT) {
+        float v[B][4];
+        long long gf[B];
+        unsigned ok[B];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int cw = cw0 + e, gj = gjs + cw;
-            const bool in = cw >= 0 && cw < W1 && (!col_edge || (gj >= 0 && gj < a.Z1)) &&
-                            !(k == k0 && rw == a.L0 - 1 && cw == a.L1 - 1);
-            v[e] = in ? -(__ldg(crow + cw) * dz) : 0.f;
-            ok |= (in ? 1u : 0u) << e;
+        for (int u = 0; u < B; u++) {
+            const int k = ts.k, rw = ts.r, j = ts.j;
+            ts.next();
+            ok[u] = 0;
+            gf[u] = 0;
+            const int gi = gi0 + rw - (a.L0 - 1);
+            if (t + u * NT >= total || gi < 0 || gi >= a.Z0) continue;
+            const long long row = (long long)k * plane + (long long)gi * a.Z1 + gjs;  // window column 0
+            const int cw0 = 4 * j - (int)(row & 3);  // window column of the group's first lane
+            if (cw0 >= W1) continue;
+            const float *crow = a.dtd + ((size_t)(k * K + k0) * W0 + rw) * W1;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int cw = cw0 + e, gj = gjs + cw;
+                const bool in = cw >= 0 && cw < W1 && (!col_edge || (gj >= 0 && gj < a.Z1)) &&
+                                !(k == k0 && rw == a.L0 - 1 && cw == a.L1 - 1);
+                v[u][e] = in ? __ldg(crow + cw) : 0.f;
+                ok[u] |= (in ? 1u : 0u) << e;
+            }
+            gf[u] = row + cw0;
         }
-        if (!ok) continue;
-        const long long gf = row + cw0;
-        if (gf >= 0 && gf + 3 < nall) {
-            red_add_v4(a.beta + gf, v[0], v[1], v[2], v[3]);
-        } else {
 #pragma unroll
-            for (int e = 0; e < 4; e++)
-                if (ok >> e & 1u) atomicAdd(a.beta + gf + e, v[e]);
+        for (int u = 0; u < B; u++) {
+            if (!ok[u]) continue;
+            float d[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) d[e] = (ok[u] >> e & 1u) ? -(v[u][e] * dz) : 0.f;
+            if (gf[u] >= 0 && gf[u] + 3 < nall) {
+                red_add_v4(a.beta + gf[u], d[0], d[1], d[2], d[3]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    if (ok[u] >> e & 1u) atomicAdd(a.beta + gf[u] + e, d[e]);
+            }
         }
     }
 }
@@ -302,7 +321,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         if constexpr (std::is_same<real, float>::value) {
             // FP32: the vector scan (beta and Z start on 16-byte boundaries,
             // checked by the host)
-            c = scan_v4<NT, RB / 3>(a, snrm, sinv, or0, oc0, r0, c0, bh, bw, use_mask && s_nz[m] == 0);
+            c = scan_v4<NT, 2>(a, snrm, sinv, or0, oc0, r0, c0, bh, bw, use_mask && s_nz[m] == 0);
         } else {
             const int nrb = (bh + kRowBlock - 1) / kRowBlock, nch = (bw + 31) >> 5, per_k = nrb * nch;
             for (int u = warp; u < K * per_k; u += NW) {
@@ -497,7 +516,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                 // beta_k[s] -= C[k][k0][s - s0] dz on V(s0) within the domain
                 const real dz = best.dz;
                 if constexpr (std::is_same<real, float>::value) {
-                    window_v4<NT>(a, k0, gi0, gj0, dz);
+                    window_v4<NT, 2>(a, k0, gi0, gj0, dz);
                 } else {
                     // the table loads of a unit first, then its reductions
                     const int W0 = a.W0, W1 = a.W1;

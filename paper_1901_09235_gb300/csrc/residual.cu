@@ -6,7 +6,7 @@
 // compacted nonzeros of Z with FP64 atomics: every nonzero (k, s, z) adds
 // -z D_k to the residual on s + Theta.  If the nonzeros do not fit the list
 // the residual is rebuilt densely instead.
-#include "common.cuh"
+#include "lgcd_global.cuh"
 
 namespace csc {
 
@@ -127,9 +127,61 @@ static int grid_for(long long n, int nt) {
     return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
 }
 
+// ------------------------------------------- beta rebuilt from the initial beta
+// beta = beta0 - sum over the nonzeros (k', s', z') of C[k][k'][s - s'] z',
+// (k, s) != (k', s'): the definition of beta (Section 3), DtX - DtD Z with
+// the diagonal term removed, evaluated from the initial beta0 = D~ * X kept
+// by the solve.  Every kernel returns at once when the nonzero list
+// overflowed; the correlation of the residual then runs instead.
+template <int NT>
+__global__ void __launch_bounds__(NT) copy_beta0_kernel(const float *src, float *dst, long long n,
+                                                         const WsHeader *h) {
+    if (h->overflow) return;
+    const long long n4 = n >> 2;  // both arrays start on 16-byte boundaries
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n4; i += (long long)gridDim.x * NT)
+        d4[i] = __ldcs(s4 + i);
+    for (long long i = 4 * n4 + (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
+        dst[i] = src[i];
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) nz_window_kernel(LgcdArgs<float> a, const int *nk, const int *ns,
+                                                        const float *nzv, const WsHeader *h, long long cap) {
+    if (h->overflow) return;
+    const long long cnt = h->nnz < cap ? h->nnz : cap;
+    for (long long e = blockIdx.x; e < cnt; e += gridDim.x) {
+        const int s = ns[e], i = s / a.Z1;
+        window_v4<NT, 2>(a, nk[e], i, s - i * a.Z1, nzv[e]);
+    }
+}
+
+// max |ST(beta, lambda) / ||D_k||^2 - Z| over every coordinate (blockIdx.y = k)
+template <int NT>
+__global__ void __launch_bounds__(NT) maxdz_kernel(const float *beta, const float *Z, const double *nrm,
+                                                    float lambda, long long plane, const WsHeader *h,
+                                                    unsigned long long *bits) {
+    if (h->overflow) return;
+    const int k = blockIdx.y;
+    const double nk = nrm[k];
+    const float nr = (float)nk, inv = (float)(1.0 / nk);
+    const float *bk = beta + (size_t)k * plane, *zk = Z + (size_t)k * plane;
+    unsigned long long m = 0;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < plane; i += (long long)gridDim.x * NT) {
+        const float z = __ldcs(zk + i);
+        float dz = coord_update(__ldcs(bk + i), lambda, nr, inv) - z;
+        dz = dz < 0.f ? -dz : dz;
+        const unsigned long long b = nonneg_bits(dz);
+        m = b > m ? b : m;
+    }
+    block_max_atomic<NT>(m, bits);
+}
+
 template <typename real>
 int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const real *X,
-                   const real *D, const real *Z, real lambda, real *beta, cudaStream_t st) {
+                   const real *D, const real *Z, real lambda, real *beta, cudaStream_t st,
+                   const real *dtd) {
     WsHeader *h = reinterpret_cast<WsHeader *>(ws + L.hdr);
     int *nk = reinterpret_cast<int *>(ws + L.nnz_k);
     int *ns = reinterpret_cast<int *>(ws + L.nnz_s);
@@ -147,11 +199,38 @@ int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const re
                                                        g.L1, g.T0, g.T1, g.Z1);
     recon_dense_kernel<real><<<grid_for(nx, 256), 256, 0, st>>>(X, Z, D, h, R, g.P, g.K, g.T0, g.T1,
                                                                 g.L0, g.L1, g.Z0, g.Z1);
+    const bool from_beta0 = beta && dtd;
+    // the FP32 residual feeds the correlation, which the beta0 form needs only
+    // after an overflow (the residual is then the dense one either way)
     residual_finish_kernel<real, 256><<<grid_for(nx, 256), 256, 0, st>>>(R, beta ? Rr : nullptr, nx,
                                                                          &h->obj_f);
     CSC_CUDA(cudaGetLastError());
-    if (beta) return launch_corr_refresh<real>(g, Rr, D, Z, nrm, lambda, beta, &h->maxdz_bits, st);
-    return CSC_OK;
+    if (!beta) return CSC_OK;
+    if constexpr (sizeof(real) == 4) {
+        if (from_beta0) {
+            const float *b0 = reinterpret_cast<const float *>(ws + L.beta0);
+            copy_beta0_kernel<256><<<grid_for(nz / 4 + 1, 256), 256, 0, st>>>(b0, beta, nz, h);
+            LgcdArgs<float> a{};
+            a.beta = beta;
+            a.Z = const_cast<float *>(Z);
+            a.dtd = dtd;
+            a.K = g.K;
+            a.Z0 = g.Z0;
+            a.Z1 = g.Z1;
+            a.L0 = g.L0;
+            a.L1 = g.L1;
+            a.W0 = g.W0;
+            a.W1 = g.W1;
+            nz_window_kernel<256><<<152 * 8, 256, 0, st>>>(a, nk, ns, nzv, h, L.nnz_cap);
+            const long long plane = g.nzpos();
+            dim3 grid((unsigned)std::min<long long>(ceil_div(plane, 256), std::max(1, 152 * 8 / g.K)), (unsigned)g.K);
+            maxdz_kernel<256><<<grid, 256, 0, st>>>(beta, Z, nrm, lambda, plane, h, &h->maxdz_bits);
+            CSC_CUDA(cudaGetLastError());
+            // overflow: the correlation of the (dense) residual instead
+            return launch_corr_refresh<real>(g, Rr, D, Z, nrm, lambda, beta, &h->maxdz_bits, st, &h->overflow);
+        }
+    }
+    return launch_corr_refresh<real>(g, Rr, D, Z, nrm, lambda, beta, &h->maxdz_bits, st);
 }
 
 int preload_residual_kernels() {
@@ -162,13 +241,17 @@ int preload_residual_kernels() {
         (const void *)scatter_kernel<float, 128>,
         (const void *)recon_dense_kernel<float>,
         (const void *)residual_finish_kernel<float, 256>,
+        (const void *)copy_beta0_kernel<256>,
+        (const void *)nz_window_kernel<256>,
+        (const void *)maxdz_kernel<256>,
     };
     return preload_functions(fns, (int)(sizeof(fns) / sizeof(fns[0])));
 }
 
 template int launch_refresh<float>(const Geom &, const WsLayout &, unsigned char *, const float *,
-                                   const float *, const float *, float, float *, cudaStream_t);
+                                   const float *, const float *, float, float *, cudaStream_t, const float *);
 template int launch_refresh<double>(const Geom &, const WsLayout &, unsigned char *, const double *,
-                                    const double *, const double *, double, double *, cudaStream_t);
+                                    const double *, const double *, double, double *, cudaStream_t,
+                                    const double *);
 
 }  // namespace csc
