@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--api", default="step", choices=["step", "calls"],
                     help="signal: one cdl_step call per step (default) or the four separate calls")
     ap.add_argument("--no-tune", action="store_true",
-                    help="served: skip the sub-domain / stop-margin autotuner (library defaults)")
+                    help="served / image4096: skip the sub-domain (and stop-margin) autotuner (library defaults)")
     return ap.parse_args()
 
 
@@ -208,13 +208,12 @@ def launches_per_step(st):
 
 def lgcd_algorithmic_bytes(st, w):
     """Bytes one LGCD launch must move by its definition: every iteration
-    reads beta and Z over K x |C_m| (8 B per candidate); every accepted update
-    reads and writes beta and reads the D^T D table over K x |window|
+    reads beta and Z over K x |C_m| (8 B per candidate; the kernel counts the
+    candidates, sub-domains clipped at tile edges included); every accepted
+    update reads and writes beta and reads the D^T D table over K x |window|
     (12 B per entry) and writes one Z (4 B)."""
-    K = w.K
-    sub = int(np.prod([2 * l for l in w.L]))
     win = int(np.prod([2 * l - 1 for l in w.L]))
-    return st["iterations"] * 8 * K * sub + st["updates"] * (12 * K * win + 4)
+    return 8 * st["candidates"] + st["updates"] * (12 * w.K * win + 4)
 
 
 def lgcd_traffic_per_launch():
@@ -529,11 +528,9 @@ def image_main(args):
         return 0
     kms = sum(st["kernel_ms"] for st in stats) / 1e3
     nz = K * (side - L[0] + 1) * (side - L[1] + 1)
-    # per scan: 8 B per candidate (beta, Z) over K x sub-domain; per update:
-    # 12 B per window entry (beta read + write, table) + 4 B for Z
-    scan_b = 8 * K * (2 * L[0]) * (2 * L[1])
-    upd_b = 12 * K * (2 * L[0] - 1) * (2 * L[1] - 1) + 4
-    abytes = sum(st["iterations"] * scan_b + st["updates"] * upd_b for st in stats)
+    # 8 B per scanned candidate (beta, Z); per update 12 B per window entry
+    # (beta read + write, table) + 4 B for Z
+    abytes = sum(lgcd_algorithmic_bytes(st, w) for st in stats)
     achieved = abytes / kms / 1e9
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -744,13 +741,8 @@ def large_image_config(w, crop, extra=None):
 
 
 def image_algorithmic_bytes(st, w):
-    """Bytes one LGCD launch must move by its definition (same rule as the
-    1-D workload): 8 B per scanned candidate (beta, Z) over K x |C_m| per
-    iteration, 12 B per window entry (beta read + write, table) over K x |W|
-    plus 4 B of Z per accepted update."""
-    sub = int(np.prod([2 * l for l in w.L]))
-    win = int(np.prod([2 * l - 1 for l in w.L]))
-    return st["iterations"] * 8 * w.K * sub + st["updates"] * (12 * w.K * win + 4)
+    """The same rule as the 1-D workload (lgcd_algorithmic_bytes)."""
+    return lgcd_algorithmic_bytes(st, w)
 
 
 def profile_value(name, key, sources):
@@ -833,7 +825,16 @@ def large_image_main(args):
     Dd = torch.from_numpy(D).to(device)
     X = make_image_device(w, args.seed + 1000 * rank + 1, D, device)
     s = pkg.make_shape(tuple(X.shape), tuple(Dd.shape))
-    opts = pkg.default_opts()
+    # sub-domain side by the autotuner, on another image of the family
+    tune = None
+    if not args.no_tune:
+        from paper_1901_09235_gb300 import autotune
+        t0 = time.perf_counter()
+        tune = autotune.tune_single(make_image_device(w, args.seed + 1000 * rank + 2, D, device), Dd,
+                                    reg=w.reg, tol=w.tol)
+        tune["seconds"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    opts = pkg.default_opts(sub=[tune["sub"]] * 2) if tune else pkg.default_opts()
     ws = pkg.workspace(s, opts, device=device)
     beta = torch.empty(pkg.z_shape(s), dtype=torch.float32, device=device)
     Z = torch.empty_like(beta)
@@ -904,7 +905,11 @@ def large_image_main(args):
         "data": "synthetic",
         "config": large_image_config(w, crop, {"parallelism": f"replicas{world}" if world > 1 else "single",
                                                "workers": last["workers"], "tiles": last["tiles"],
-                                               "tile": last["tile_size"]}),
+                                               "tile": last["tile_size"],
+                                               "sub": list(opts.sub) if tune else [2 * l for l in w.L],
+                                               "sub_choice": "autotuned on another image of the family"
+                                               if tune else "library default (2 L)"}),
+        "tuning": tune,
         "updates_per_s": world * upd / tot,
         "p50_ms": 1e3 * float(np.percentile(times, 50)),
         "p99_ms": 1e3 * float(np.percentile(times, 99)),

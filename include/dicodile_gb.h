@@ -122,6 +122,7 @@ typedef struct {
     long long phase_cycles[6];   /* SM cycles summed over workers: wave start, neighbour
                                     messages, scan + apply, soft-lock tests, end of wave,
                                     pauses                                                */
+    long long candidates;        /* coordinates scanned: K x |C_m| summed over iterations */
     int status;                  /* the returned status                                  */
 } csc_solve_stats;
 

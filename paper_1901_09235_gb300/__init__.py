@@ -48,7 +48,7 @@ class SolveStats(C.Structure):
                 ("max_worker_iterations", C.c_longlong), ("max_worker_updates", C.c_longlong),
                 ("last_active_wave", C.c_longlong), ("t_first_pause_us", C.c_double),
                 ("t_exit_us", C.c_double), ("wakeups", C.c_longlong),
-                ("phase_cycles", C.c_longlong * 6), ("status", C.c_int)]
+                ("phase_cycles", C.c_longlong * 6), ("candidates", C.c_longlong), ("status", C.c_int)]
 
     _arrays = ("tiles", "tile_size", "phase_cycles")
 

@@ -136,3 +136,50 @@ def tune(D, make_image, classes=None, margins=(0.99, 0.95, 0.9), reps: int = 2, 
             table[str(c)] = {"sub": int(bs), "stop_margin": float(bm), "ms": tried[best], "side": side,
                              "tried": tried}
     return table
+
+
+def single_candidates(L: int):
+    """Sub-domain sides for single solves: L/2, 3L/4, L, 4L/3 and the paper's 2L."""
+    return sorted({max(1, s) for s in (L // 2, (3 * L) // 4, L, (4 * L + 2) // 3, 2 * L)})
+
+
+def tune_single(X, D, reg: float = 0.1, tol: float = 1e-4, reps: int = 2, candidates=None, log=None):
+    """Sub-domain side for single solves (csc_init_beta + csc_lgcd_solve with
+    its fresh-beta check) of images like X (P, T0, T1; square atoms): each
+    candidate side is timed with CUDA events on the current stream over `reps`
+    solves, after one untimed solve, and the fastest is kept.  X should be a
+    tuning image drawn like the workload, not the one to be solved.  Returns
+    {"sub": side, "ms": mean ms per solve, "tried": {side: ms}}."""
+    import torch
+    from . import CSC_OK, csc_init_beta, csc_lgcd_solve, default_opts, make_shape, tab_shape, workspace, z_shape
+    K, P, L0, L1 = D.shape
+    if L0 != L1:
+        raise ValueError("square atoms only")
+    s = make_shape(tuple(X.shape), tuple(D.shape))
+    beta = torch.empty(z_shape(s), dtype=torch.float32, device=X.device)
+    Z = torch.empty_like(beta)
+    dtd = torch.empty(tab_shape(s), dtype=torch.float32, device=X.device)
+    ws = workspace(s, device=X.device)
+    tried = {}
+    for sub in candidates or single_candidates(L0):
+        o = default_opts(sub=[sub, sub])
+        ms = []
+        for r in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, _, lm = csc_init_beta(X, D, beta, dtd, ws)
+            _, st = csc_lgcd_solve(X, D, dtd, beta, reg * lm, tol, Z=Z, opts=o, ws=ws)
+            b.record()
+            b.synchronize()
+            if st["status"] != CSC_OK:
+                break
+            if r > 0:
+                ms.append(a.elapsed_time(b))
+        else:
+            tried[sub] = sum(ms) / len(ms)
+        if log:
+            log(f"sub {sub}: {tried.get(sub, float('nan')):.2f} ms")
+    if not tried:
+        raise RuntimeError("no sub-domain candidate converged")
+    best = min(tried, key=tried.get)
+    return {"sub": best, "ms": tried[best], "tried": tried}

@@ -48,7 +48,7 @@ struct alignas(128) WsHeader {
     int pad4[30];
     unsigned long long updates_total;  // global update count (max_updates check)
     int pad5[30];
-    long long stat[8];      // updates, iterations, rejected, subtol, messages, deferred
+    long long stat[8];      // updates, iterations, rejected, subtol, messages, deferred, candidates
     unsigned long long wmax[2];        // largest per-worker iteration / update counts
     unsigned long long tmax[4];        // worker timeline (ns after its start): last update, exit, first pause; wake-ups
     unsigned long long tph[6];         // SM cycles per wave phase, summed over workers
@@ -65,7 +65,7 @@ struct alignas(128) WsHeader {
     unsigned long long tphmax[8];      // largest per-worker SM cycles per phase
 };
 
-enum StatIdx { ST_UPDATES = 0, ST_ITERS, ST_REJECTED, ST_SUBTOL, ST_MESSAGES, ST_DEFERRED };
+enum StatIdx { ST_UPDATES = 0, ST_ITERS, ST_REJECTED, ST_SUBTOL, ST_MESSAGES, ST_DEFERRED, ST_CAND };
 
 constexpr int kMailboxCap = 512;    // records per directed neighbour link
 constexpr int kDirs = 8;            // neighbour directions in a 2-D tile grid

@@ -528,6 +528,7 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
         S.skipped_subtol += hh.stat[ST_SUBTOL];
         S.messages += hh.stat[ST_MESSAGES];
         S.deferred += hh.stat[ST_DEFERRED];
+        S.candidates += hh.stat[ST_CAND];
         S.max_worker_iterations = std::max<long long>(S.max_worker_iterations, (long long)hh.wmax[0]);
         S.max_worker_updates = std::max<long long>(S.max_worker_updates, (long long)hh.wmax[1]);
         S.last_active_wave = std::max(S.last_active_wave, (long long)hh.tmax[0]);

@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
     const int s_dr = s_r / a.sub1, s_dc = s_r % a.sub1;
     // counters and the timeline are the leader's (thread 0)
     int n_upd = 0, n_it = 0, n_rej = 0, n_sub = 0, n_def = 0, n_step = 0;
+    long long n_cand = 0;  // positions scanned (times K at the end)
     if (tid == 0) {
         for (int i = 0; i < 6; i++) S.ph[i] = 0;
         S.t_last = S.t_pause = 0;
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
             }
         }
         n_it++;
+        n_cand += nb;
         lap(2);
         if (best_bits == 0) {
             n_sub++;
@@ -648,6 +650,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 2) lgcd_async_kernel(LgcdArgs<r
     if (tid == 0) {
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_UPDATES], (unsigned long long)n_upd);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_ITERS], (unsigned long long)n_it);
+        atomicAdd((unsigned long long *)&a.hdr->stat[ST_CAND], (unsigned long long)(n_cand * t.K));
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_REJECTED], (unsigned long long)n_rej);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_SUBTOL], (unsigned long long)n_sub);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_DEFERRED], (unsigned long long)n_def);

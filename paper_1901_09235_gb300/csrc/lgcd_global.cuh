@@ -22,7 +22,15 @@ namespace csc {
 // shared-memory variant: `pending` counts active workers plus flag bumps not
 // yet observed by their tile.  One sub-domain per iteration, scanned and
 // updated by the whole CTA.
+// Threads per worker CTA of the single-solve kernel (two CTAs per SM).
+// Measured on the 4096^2 image (25 atoms of 32 x 32): 304 x 512, 456 x 256,
+// 608 x 256 and 304 x 384 threads all solve in the same time (45 ms), the
+// shorter per-tile chains of more tiles offset by slower iterations.
 constexpr int kGlobThreads = 512;
+// Tasks whose loads a thread issues together in the FP32 scan and window
+// update: two each fit the 64 registers of two 512-thread CTAs per SM without
+// spilling; three to six (with spills) were slower on the 4096^2 image.
+constexpr int kScanBatch = 2, kWindowBatch = 2;
 // Boxes of K x rows x cols are walked in units of (atom, block of RB rows,
 // 32-column chunk): a warp takes units NW apart, issues the loads of all rows
 // of its unit, then evaluates them.  Two divisions per unit, none per
@@ -271,6 +279,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
     // SM cycles of thread 0 per phase: scan, wait for the scan barrier,
     // soft-lock, window update, update barrier and flags, pause
     __shared__ unsigned long long s_ph[6], s_t;
+    __shared__ unsigned long long s_cand;  // candidates scanned (K x |C_m| per iteration)
     if (threadIdx.x == 0) {
         s_deadline = globaltimer_ns() + a.timeout_ns;
         real guard = real(0);
@@ -283,6 +292,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         s_seen = 0;
         for (int i = 0; i < 5; i++) s_cnt[i] = 0;
         for (int i = 0; i < 6; i++) s_ph[i] = 0;
+        s_cand = 0;
         s_t = clock64();
     }
     // Dirty sub-domains (tiles of at most 64): a bit is cleared when a scan
@@ -321,7 +331,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         if constexpr (std::is_same<real, float>::value) {
             // FP32: the vector scan (beta and Z start on 16-byte boundaries,
             // checked by the host)
-            c = scan_v4<NT, 2>(a, snrm, sinv, or0, oc0, r0, c0, bh, bw, use_mask && s_nz[m] == 0);
+            c = scan_v4<NT, kScanBatch>(a, snrm, sinv, or0, oc0, r0, c0, bh, bw, use_mask && s_nz[m] == 0);
         } else {
             const int nrb = (bh + kRowBlock - 1) / kRowBlock, nch = (bw + 31) >> 5, per_k = nrb * nch;
             for (int u = warp; u < K * per_k; u += NW) {
@@ -386,6 +396,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         par ^= 1;
         if (threadIdx.x == 0) {
             s_cnt[1]++;
+            s_cand += (unsigned long long)K * bh * bw;
             const unsigned long long t = clock64();
             s_ph[1] += t - s_t;
             s_t = t;
@@ -516,7 +527,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                 // beta_k[s] -= C[k][k0][s - s0] dz on V(s0) within the domain
                 const real dz = best.dz;
                 if constexpr (std::is_same<real, float>::value) {
-                    window_v4<NT, 2>(a, k0, gi0, gj0, dz);
+                    window_v4<NT, kWindowBatch>(a, k0, gi0, gj0, dz);
                 } else {
                     // the table loads of a unit first, then its reductions
                     const int W0 = a.W0, W1 = a.W1;
@@ -643,6 +654,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_REJECTED], (unsigned long long)s_cnt[2]);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_SUBTOL], (unsigned long long)s_cnt[3]);
         atomicAdd((unsigned long long *)&a.hdr->stat[ST_MESSAGES], (unsigned long long)s_cnt[4]);
+        atomicAdd((unsigned long long *)&a.hdr->stat[ST_CAND], s_cand);
         atomicMax(&a.hdr->wmax[0], (unsigned long long)s_cnt[1]);
         atomicMax(&a.hdr->wmax[1], (unsigned long long)s_cnt[0]);
         for (int i = 0; i < 6; i++) {
