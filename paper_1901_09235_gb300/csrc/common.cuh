@@ -255,6 +255,10 @@ int read_back(T *dst, const void *src_dev, cudaStream_t st) {
 // running: a first launch beside a persistent kernel would then stall until
 // the persistent kernel ends.
 int preload_corr_kernels();
+// Queues whose persistent kernel is running (created and not yet closed).
+// Kernels launched beside one must fit the registers it leaves free on each
+// SM sub-partition; the 2-D FP32 correlations then take their smaller shape.
+int live_queues();
 int preload_residual_kernels();
 int preload_umma_kernels();
 int preload_functions(const void *const *fns, int n);

@@ -124,8 +124,9 @@ __global__ void __launch_bounds__(NT) corr_kernel(CorrArgs<real> a) {
 // + q).  Taps go in blocks of NQ along a tap row: the 2 NQ signal values of
 // row i0 + r + tau0 held in registers serve the NQ x NQ products of every
 // atom, so each shared-memory word feeds NQ KC FMAs.  Weights are staged
-// tap-major (the KC atoms of a tap contiguous, a broadcast), tap columns
-// padded with zero weights to a multiple of NQ.  Every output accumulates
+// tap-major (the KC atoms of a tap contiguous, padded to KCP = a multiple of
+// four, read as 16-byte broadcasts), tap columns padded with zero weights to a
+// multiple of NQ.  Every output accumulates
 // channel by channel, tap row by tap row and tap by tap, as corr_kernel does.
 template <int NT, int TR, int NQ, int KC, int EPI>
 __global__ void __launch_bounds__(NT) corr_rows_kernel(CorrArgs<float> a) {
@@ -133,9 +134,10 @@ __global__ void __launch_bounds__(NT) corr_rows_kernel(CorrArgs<float> a) {
     constexpr int TPR = NT / TR, TC = TPR * NQ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L0 = a.L0, L1 = a.L1, Lp = (L1 + NQ - 1) / NQ * NQ;
+    constexpr int KCP = (KC + 3) / 4 * 4;
     const int PR = TR + L0 - 1, PC = (TC + Lp + NQ + 3) / 4 * 4;  // patch rows, padded row length
     float *sS = reinterpret_cast<float *>(smem_raw);  // PR x PC signal patch
-    float *sW = sS + (size_t)PR * PC;                  // L0 x Lp x KC weights
+    float *sW = sS + (size_t)PR * PC;                  // L0 x Lp x KCP weights
     const int i0 = blockIdx.y * TR, j0 = blockIdx.x * TC, k0 = blockIdx.z * KC;
     const int r = threadIdx.x / TPR, s0 = (threadIdx.x % TPR) * NQ;
     float acc[KC][NQ];
@@ -150,14 +152,14 @@ __global__ void __launch_bounds__(NT) corr_rows_kernel(CorrArgs<float> a) {
             const int rr = e / PC, cc = e - rr * PC, gi = i0 + rr, gj = j0 + cc;
             sS[e] = (gi < a.T0 && gj < a.T1) ? Sp[(size_t)gi * a.T1 + gj] : 0.f;
         }
-        for (int e = threadIdx.x; e < L0 * Lp * KC; e += NT) {
-            const int tt = e / KC, kk = e - tt * KC, ta = tt / Lp, tb = tt - ta * Lp, k = k0 + kk;
-            sW[e] = (tb < L1 && k < a.K) ? a.Wt[(((size_t)k * a.P + p) * L0 + ta) * L1 + tb] : 0.f;
+        for (int e = threadIdx.x; e < L0 * Lp * KCP; e += NT) {
+            const int tt = e / KCP, kk = e - tt * KCP, ta = tt / Lp, tb = tt - ta * Lp, k = k0 + kk;
+            sW[e] = (kk < KC && tb < L1 && k < a.K) ? a.Wt[(((size_t)k * a.P + p) * L0 + ta) * L1 + tb] : 0.f;
         }
         __syncthreads();
         for (int ta = 0; ta < L0; ta++) {
             const float *row = sS + (size_t)(r + ta) * PC + s0;
-            const float *wta = sW + (size_t)ta * Lp * KC;
+            const float *wta = sW + (size_t)ta * Lp * KCP;
             for (int tb = 0; tb < Lp; tb += NQ) {
                 float x[2 * NQ];
 #pragma unroll
@@ -170,12 +172,20 @@ __global__ void __launch_bounds__(NT) corr_rows_kernel(CorrArgs<float> a) {
                 }
 #pragma unroll
                 for (int u = 0; u < NQ; u++) {
-                    const float *wt = wta + (tb + u) * KC;
+                    const float4 *wt = reinterpret_cast<const float4 *>(wta + (tb + u) * KCP);
+                    float w[KCP];
+#pragma unroll
+                    for (int g = 0; g < KCP / 4; g++) {
+                        const float4 v = wt[g];
+                        w[4 * g] = v.x;
+                        w[4 * g + 1] = v.y;
+                        w[4 * g + 2] = v.z;
+                        w[4 * g + 3] = v.w;
+                    }
 #pragma unroll
                     for (int kk = 0; kk < KC; kk++) {
-                        const float wv = wt[kk];
 #pragma unroll
-                        for (int q = 0; q < NQ; q++) acc[kk][q] = fmaf(wv, x[q + u], acc[kk][q]);
+                        for (int q = 0; q < NQ; q++) acc[kk][q] = fmaf(w[kk], x[q + u], acc[kk][q]);
                     }
                 }
             }
@@ -223,7 +233,7 @@ static int run_corr_rows(const Geom &g, CorrArgs<float> a, cudaStream_t st) {
     auto kern = corr_rows_kernel<NT, TR, NQ, KC, EPI>;
     const int Lp = (g.L1 + NQ - 1) / NQ * NQ;
     const int PR = TR + g.L0 - 1, PC = (TC + Lp + NQ + 3) / 4 * 4;
-    const size_t smem = ((size_t)PR * PC + (size_t)g.L0 * Lp * KC) * sizeof(float);
+    const size_t smem = ((size_t)PR * PC + (size_t)g.L0 * Lp * ((KC + 3) / 4 * 4)) * sizeof(float);
     if (smem > 227 * 1024) return CSC_ERR_UNIMPLEMENTED;
     if (smem > 48 * 1024)
         CSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -243,12 +253,22 @@ static int corr_rows_dispatch(const Geom &g, CorrArgs<float> a, cudaStream_t st)
         if (g.K <= 10) return run_corr_rows<128, 1, 4, 10, EPI>(g, a, st);
         return run_corr_rows<128, 1, 4, 16, EPI>(g, a, st);
     }
-    // 2-D: 4 rows x 128 columns per CTA; the atom chunk (8, 13 or 16) that
-    // pads K least (25 atoms: two chunks of 13)
-    if (g.K <= 8) return run_corr_rows<128, 4, 4, 8, EPI>(g, a, st);
+    // 2-D: 8 rows x 128 columns per CTA of 256 threads (4 positions each);
+    // the atom chunk (8, 13 or 16) that pads K least (25 atoms: two chunks of
+    // 13).  On the 4096^2 image with 25 atoms of 32 x 32: 15.8 ms against
+    // 19.6-19.8 ms for 128 threads x 4 rows, 16.1 for 512 x 16 rows, 16.9 for
+    // 384 x 12 rows, 20.6-21.9 with 8 positions a thread.  Beside a running
+    // queue kernel only one warp of 128 registers fits per SM sub-partition:
+    // 128 threads x 4 rows then.
     const long long w13 = ceil_div(g.K, 13) * 13, w16 = ceil_div(g.K, 16) * 16;
-    if (w13 < w16) return run_corr_rows<128, 4, 4, 13, EPI>(g, a, st);
-    return run_corr_rows<128, 4, 4, 16, EPI>(g, a, st);
+    if (live_queues() > 0) {
+        if (g.K <= 8) return run_corr_rows<128, 4, 4, 8, EPI>(g, a, st);
+        if (w13 < w16) return run_corr_rows<128, 4, 4, 13, EPI>(g, a, st);
+        return run_corr_rows<128, 4, 4, 16, EPI>(g, a, st);
+    }
+    if (g.K <= 8) return run_corr_rows<256, 8, 4, 8, EPI>(g, a, st);
+    if (w13 < w16) return run_corr_rows<256, 8, 4, 13, EPI>(g, a, st);
+    return run_corr_rows<256, 8, 4, 16, EPI>(g, a, st);
 }
 
 template <typename real, int NT, int TR, int NQ, int KC, int EPI>
@@ -397,6 +417,9 @@ int preload_corr_kernels() {
         (const void *)corr_rows_kernel<128, 4, 4, 8, EPI_INIT>,
         (const void *)corr_rows_kernel<128, 4, 4, 13, EPI_INIT>,
         (const void *)corr_rows_kernel<128, 4, 4, 16, EPI_INIT>,
+        (const void *)corr_rows_kernel<256, 8, 4, 8, EPI_INIT>,
+        (const void *)corr_rows_kernel<256, 8, 4, 13, EPI_INIT>,
+        (const void *)corr_rows_kernel<256, 8, 4, 16, EPI_INIT>,
         (const void *)corr_rows_kernel<128, 1, 4, 4, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 1, 4, 8, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 1, 4, 10, EPI_REFRESH>,
@@ -404,6 +427,9 @@ int preload_corr_kernels() {
         (const void *)corr_rows_kernel<128, 4, 4, 8, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 4, 4, 13, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 4, 4, 16, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<256, 8, 4, 8, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<256, 8, 4, 13, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<256, 8, 4, 16, EPI_REFRESH>,
         (const void *)dtd_kernel<float, 256>,
         (const void *)atom_norm_kernel<float, 256>,
     };

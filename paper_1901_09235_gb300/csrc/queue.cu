@@ -19,6 +19,7 @@
 // host polls without CUDA calls.  A close word ends the kernel once the queue
 // is empty.  Every wait is bounded by the kernel's deadline.
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "lgcd_global.cuh"
@@ -206,6 +207,9 @@ static QueueLayout queue_layout(const Geom &g, int max_jobs, int ctl_slots, int 
     return L;
 }
 
+static std::atomic<int> g_live_queues{0};
+int live_queues() { return g_live_queues.load(); }
+
 static int queue_grid(int ctas_per_sm) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -341,6 +345,7 @@ int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, c
     if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(kQueueThreads), args, smem, q->kstream)) != cudaSuccess)
         return fail(e);
     *out = q;
+    g_live_queues.fetch_add(1);
     return CSC_OK;
 }
 
@@ -497,6 +502,7 @@ int csc_queue_close(csc_queue *q) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->kstream);
     if (e != cudaSuccess) rc = set_cuda_error(e);
     delete q;
+    g_live_queues.fetch_sub(1);
     return rc;
 }
 

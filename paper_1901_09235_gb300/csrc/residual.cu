@@ -157,7 +157,14 @@ __global__ void __launch_bounds__(NT) nz_window_kernel(LgcdArgs<float> a, const 
     }
 }
 
-// max |ST(beta, lambda) / ||D_k||^2 - Z| over every coordinate (blockIdx.y = k)
+// max |ST(beta, lambda) / ||D_k||^2 - Z| over every coordinate (blockIdx.y = k):
+// the aligned groups of four inside atom k's plane by 16-byte loads, the few
+// elements before the first and after the last group one by one
+__device__ __forceinline__ unsigned long long dz_bits(float b, float z, float lambda, float nr, float inv) {
+    float dz = coord_update(b, lambda, nr, inv) - z;
+    return nonneg_bits(dz < 0.f ? -dz : dz);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) maxdz_kernel(const float *beta, const float *Z, const double *nrm,
                                                     float lambda, long long plane, const WsHeader *h,
@@ -166,14 +173,30 @@ __global__ void __launch_bounds__(NT) maxdz_kernel(const float *beta, const floa
     const int k = blockIdx.y;
     const double nk = nrm[k];
     const float nr = (float)nk, inv = (float)(1.0 / nk);
-    const float *bk = beta + (size_t)k * plane, *zk = Z + (size_t)k * plane;
+    const long long beg = (long long)k * plane, end = beg + plane;
+    const long long g0 = (beg + 3) >> 2, g1 = end >> 2;  // whole groups [g0, g1)
+    const float4 *b4 = reinterpret_cast<const float4 *>(beta), *z4 = reinterpret_cast<const float4 *>(Z);
     unsigned long long m = 0;
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < plane; i += (long long)gridDim.x * NT) {
-        const float z = __ldcs(zk + i);
-        float dz = coord_update(__ldcs(bk + i), lambda, nr, inv) - z;
-        dz = dz < 0.f ? -dz : dz;
-        const unsigned long long b = nonneg_bits(dz);
-        m = b > m ? b : m;
+    for (long long g = g0 + (long long)blockIdx.x * NT + threadIdx.x; g < g1; g += (long long)gridDim.x * NT) {
+        const float4 b = __ldcs(b4 + g), z = __ldcs(z4 + g);
+        unsigned long long v = dz_bits(b.x, z.x, lambda, nr, inv);
+        unsigned long long u = dz_bits(b.y, z.y, lambda, nr, inv);
+        v = u > v ? u : v;
+        u = dz_bits(b.z, z.z, lambda, nr, inv);
+        v = u > v ? u : v;
+        u = dz_bits(b.w, z.w, lambda, nr, inv);
+        v = u > v ? u : v;
+        m = v > m ? v : m;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 8) {
+        // up to three elements before the first whole group and three after the last
+        const long long i = threadIdx.x < 4 ? beg + threadIdx.x : 4 * (g1 > g0 ? g1 : g0) + (threadIdx.x - 4);
+        const bool head = threadIdx.x < 4 && i < 4 * g0 && i < end;
+        const bool tail = threadIdx.x >= 4 && i >= 4 * g0 && i < end;
+        if (head || tail) {
+            const unsigned long long v = dz_bits(beta[i], Z[i], lambda, nr, inv);
+            m = v > m ? v : m;
+        }
     }
     block_max_atomic<NT>(m, bits);
 }
@@ -223,7 +246,7 @@ int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const re
             a.W1 = g.W1;
             nz_window_kernel<256><<<152 * 8, 256, 0, st>>>(a, nk, ns, nzv, h, L.nnz_cap);
             const long long plane = g.nzpos();
-            dim3 grid((unsigned)std::min<long long>(ceil_div(plane, 256), std::max(1, 152 * 8 / g.K)), (unsigned)g.K);
+            dim3 grid((unsigned)std::min<long long>(ceil_div(plane, 4 * 256), std::max(1, 152 * 8 / g.K)), (unsigned)g.K);
             maxdz_kernel<256><<<grid, 256, 0, st>>>(beta, Z, nrm, lambda, plane, h, &h->maxdz_bits);
             CSC_CUDA(cudaGetLastError());
             // overflow: the correlation of the (dense) residual instead
