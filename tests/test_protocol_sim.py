@@ -1,0 +1,82 @@
+"""The worker protocol of the global-memory LGCD tiles (Alg. 3: soft-locks,
+notifications, the `pending` termination count), run on the CPU model of
+tests/_protocol_sim.py under schedules the GPU never promises: seeded
+random interleavings of every worker step (a neighbour can see half of a
+window update), notifications delayed by up to 200 steps, lock-step rounds
+in which every worker scans before any applies.
+
+* With soft-locks every run terminates with nothing pending and nothing in
+  flight, at max |dZ| < eps on a beta recomputed from scratch, at the FP64
+  oracle's objective (Alg. 1 on one worker) within 1e-9 relative.
+* Without them (the ablation of Section 5.1), four workers updating around
+  each tile corner at once interfere (Prop. A.2) and the activations grow
+  until the divergence guard stops the run, while the soft-locks on the same
+  lock-step schedule converge to the oracle's optimum."""
+import numpy as np
+import pytest
+
+from synthetic import Workload, make_problem
+from tests._protocol_sim import Problem, Sim
+
+W1 = Workload("sim1d", P=2, K=3, T=(300,), L=(8,), density=0.05, sigma=0.1)
+W2 = Workload("sim2d", P=1, K=2, T=(40, 44), L=(4, 4), density=0.04, sigma=0.1)
+EPS = 1e-6
+
+CASES = [
+    (W1, (16,), "random", 0, 20), (W1, (8,), "random", 1, 200), (W1, (8,), "lockstep", 0, 1),
+    (W2, (8, 8), "random", 2, 20), (W2, (4, 5), "random", 3, 200), (W2, (4, 5), "lockstep", 0, 1),
+]
+
+
+@pytest.mark.parametrize("w,tile,schedule,seed,delay", CASES,
+                         ids=[f"{c[0].name}-{'x'.join(map(str, c[1]))}-{c[2]}{c[3]}" for c in CASES])
+def test_soft_locks_terminate_at_the_oracle_optimum(orc, w, tile, schedule, seed, delay):
+    X, D, _ = make_problem(w, 1)
+    lam = 0.1 * orc.lambda_max(X, D)
+    pb = Problem(X, D, lam, EPS)
+    sim = Sim(pb, tile=tile, sub=tuple(2 * l for l in w.L), lock=True, schedule=schedule, seed=seed,
+              max_delay=delay)
+    sim.run()
+    assert sim.stop is None
+    assert sim.pending == 0 and not sim.in_flight and sim.G > 4
+    # border candidates met competition and the lock decided
+    assert sim.lock_checks > 0 and sim.rejected > 0 and sim.accept_log
+    assert all(d0 > lo and d0 >= hi for d0, lo, hi in sim.accept_log)
+    assert pb.kkt(sim.Z) < EPS * (1 + 1e-9)
+    ref = orc.lgcd(X, D, lam, EPS)
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    assert abs(pb.objective(sim.Z) - f_ref) <= 1e-9 * f_ref
+
+
+def _corner_problem():
+    """One 4 x 4 box atom; activations of 5 at every tile corner of a 4 x 4
+    tile grid, so the four tiles around a corner all find their best
+    candidate next to it."""
+    from scipy.signal import convolve
+    L, T = 4, 36
+    D = np.ones((1, 1, L, L)) / L
+    Zt = np.zeros((T - L + 1, T - L + 1))
+    for ci in range(4, 33, 4):
+        for cj in range(4, 33, 4):
+            Zt[ci - 2, cj - 2] = 5.0
+    X = convolve(Zt, D[0, 0], mode="full")[None] + 0.01 * np.random.default_rng(0).standard_normal((1, T, T))
+    return X, D, L
+
+
+def test_without_soft_locks_corner_updates_diverge(orc):
+    X, D, L = _corner_problem()
+    lam = 0.01 * orc.lambda_max(X, D)
+    pb = Problem(X, D, lam, EPS)
+    guard = 50.0 / np.abs(D).max()  # the bound of Section 5.1
+    nolock = Sim(pb, tile=(L, L), sub=(2 * L, 2 * L), lock=False, schedule="lockstep", guard=guard)
+    nolock.run(max_ticks=40000)
+    assert nolock.stop == "diverged"
+    assert np.abs(nolock.Z).max() > guard
+    assert pb.objective(nolock.Z) > pb.objective(np.zeros_like(nolock.Z))
+    locked = Sim(pb, tile=(L, L), sub=(2 * L, 2 * L), lock=True, schedule="lockstep", guard=guard)
+    locked.run(max_ticks=200000)
+    assert locked.stop is None and locked.pending == 0
+    assert pb.kkt(locked.Z) < EPS * (1 + 1e-9)
+    ref = orc.lgcd(X, D, lam, EPS)
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    assert abs(pb.objective(locked.Z) - f_ref) <= 1e-9 * f_ref
