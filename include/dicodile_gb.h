@@ -322,6 +322,26 @@ CSC_API int csc_queue_create(const csc_shape *atoms, const float *D, const float
                              size_t host_bytes, double run_seconds, csc_stream_t kernel_stream,
                              csc_stream_t side_stream, csc_queue **queue_out);
 
+/* csc_queue_create without starting the kernel: jobs may then be submitted
+ * (csc_queue_submit) before csc_queue_start launches it.  With every job
+ * published before the launch, the queue needs no concurrency between the
+ * host's copies and the running kernel -- it runs the same way when kernels
+ * are serialised (a profiler that replays them one at a time).  Same
+ * arguments, ownership and errors as csc_queue_create. */
+CSC_API int csc_queue_create_deferred(const csc_shape *atoms, const float *D, const float *dtd,
+                                      const csc_solve_opts *opts, int max_jobs, int ctl_slots,
+                                      int ctas_per_sm, void *device_workspace, size_t device_bytes,
+                                      void *host_workspace, size_t host_bytes, double run_seconds,
+                                      csc_stream_t kernel_stream, csc_stream_t side_stream,
+                                      csc_queue **queue_out);
+
+/* Launch the kernel of a queue made by csc_queue_create_deferred.  drain = 1:
+ * the kernel ends by itself once every job submitted before this call is done,
+ * and later csc_queue_submit calls return CSC_ERR_INVALID; drain = 0: the
+ * kernel keeps taking jobs until csc_queue_close, as after csc_queue_create.
+ * CSC_ERR_INVALID for a queue already running or another drain value. */
+CSC_API int csc_queue_start(csc_queue *queue, int drain);
+
 /* Queue one image of T0 x T1 samples: beta [K][Z0][Z1] must hold D~ * X (from
  * csc_init_beta, or a consistent warm state with warm_start = 1, in which
  * case Z is kept; otherwise Z is zeroed).  beta and Z belong to the caller and
@@ -346,7 +366,7 @@ CSC_API int csc_queue_poll(csc_queue *queue, int job, csc_solve_stats *stats);
 CSC_API int csc_queue_inspect(csc_queue *queue, int job, long long *out);
 
 /* No more jobs: wait until the queue drains, stop the kernel, release the
- * handle. */
+ * handle (a queue that was never started: just the handle). */
 CSC_API int csc_queue_close(csc_queue *queue);
 
 /* FP64 variants of csc_init_beta and csc_lgcd_solve (same layouts, double

@@ -106,6 +106,8 @@ def load():
         "csc_rcd_solve": (i, [S, p, p, p, p, C.c_float, p, C.c_longlong, C.POINTER(C.c_longlong), p, sz, p]),
         "csc_queue_workspace_size": (i, [S, i, i, i, C.POINTER(sz), C.POINTER(sz)]),
         "csc_queue_create": (i, [S, p, p, O, i, i, i, p, sz, p, sz, d, p, p, C.POINTER(p)]),
+        "csc_queue_create_deferred": (i, [S, p, p, O, i, i, i, p, sz, p, sz, d, p, p, C.POINTER(p)]),
+        "csc_queue_start": (i, [p, i]),
         "csc_queue_submit": (i, [p, i, i, p, p, C.c_float, C.c_float, i, O, C.POINTER(i)]),
         "csc_queue_poll": (i, [p, i, ST]),
         "csc_queue_close": (i, [p]),
@@ -343,10 +345,13 @@ class Queue:
     the legacy default stream of a blocking stream): the kernel ends only on
     close() or after run_seconds.  ctas_per_sm: 2 (0, the default) leaves room
     beside the queue for the tensor-core beta-init; 3 runs more tiles at once
-    and leaves room for the FP32 calls only."""
+    and leaves room for the FP32 calls only.  start=False makes the queue
+    without launching its kernel: jobs submitted before start() are published
+    before it runs, and start(drain=True) lets it end by itself once they are
+    done (no host copy has to overlap the running kernel)."""
 
     def __init__(self, D, dtd, max_jobs: int = 1024, ctl_slots: int = 256, run_seconds: float = 120.0,
-                 opts: SolveOpts | None = None, ctas_per_sm: int = 0):
+                 opts: SolveOpts | None = None, ctas_per_sm: int = 0, start: bool = True):
         import torch
         _need(D, torch.float32, "D")
         _need(dtd, torch.float32, "dtd")
@@ -370,13 +375,21 @@ class Queue:
         self._opts = opts
         self._jobs = {}
         h = C.c_void_p(0)
-        _check(lib.csc_queue_create(C.byref(s), _ptr(D), _ptr(dtd), C.byref(opts) if opts else None,
-                                    int(max_jobs), int(ctl_slots), int(ctas_per_sm), _ptr(self.ws),
-                                    self.ws.numel(),
-                                    C.c_void_p(self.host.data_ptr()), self.host.numel(), float(run_seconds),
-                                    C.c_void_p(self.kernel_stream.cuda_stream),
-                                    C.c_void_p(self.side_stream.cuda_stream), C.byref(h)), "csc_queue_create")
+        create = lib.csc_queue_create if start else lib.csc_queue_create_deferred
+        _check(create(C.byref(s), _ptr(D), _ptr(dtd), C.byref(opts) if opts else None,
+                      int(max_jobs), int(ctl_slots), int(ctas_per_sm), _ptr(self.ws), self.ws.numel(),
+                      C.c_void_p(self.host.data_ptr()), self.host.numel(), float(run_seconds),
+                      C.c_void_p(self.kernel_stream.cuda_stream), C.c_void_p(self.side_stream.cuda_stream),
+                      C.byref(h)), "csc_queue_create")
         self._h = h
+
+    def start(self, drain: bool = True):
+        """Launch the kernel of a queue made with start=False (csc_queue_start).
+        drain: it ends by itself after the jobs submitted so far, and takes no
+        more."""
+        if self._h is None:
+            raise RuntimeError("queue closed")
+        _check(load().csc_queue_start(self._h, int(bool(drain))), "csc_queue_start")
 
     def submit(self, beta, Z, lam: float, tol: float, warm_start: bool = False, stream=None,
                opts: SolveOpts | None = None) -> int:

@@ -33,6 +33,8 @@ struct QueueCtl {       // device control words (host-written njobs / close)
     int pad1[31];
     int slot;           // next slot to take
     int pad2[31];
+    int drain;          // 1: every job was published before the launch; a CTA
+    int pad3[31];       //    whose slot lies past the last job's tiles exits
 };
 
 struct QueueJob {       // device job table entry
@@ -112,6 +114,10 @@ __global__ void __maxnreg__(REGS) lgcd_queue_kernel(QueueCtl *qc, QueueJob *jobs
                     state = 1;
                     break;
                 }
+                if (ld_relaxed(&qc->drain)) {  // no job will follow: nothing left for slot s
+                    state = 1;
+                    break;
+                }
                 if (globaltimer_ns() > t_end) {
                     state = 2;
                     break;
@@ -180,6 +186,10 @@ struct Queue {
     std::vector<int> free_ctl;
     csc_solve_opts opts;
     cudaStream_t kstream = nullptr, sstream = nullptr;
+    // deferred start: the kernel's launch arguments, kept until csc_queue_start
+    bool launched = false, drain = false;
+    const void *kern = nullptr;
+    unsigned long long run_ns = 0;
 };
 
 static size_t q_align(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -259,10 +269,25 @@ int csc_queue_workspace_size(const csc_shape *atoms, int max_jobs, int ctl_slots
     return CSC_OK;
 }
 
-int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, const csc_solve_opts *opts,
-                     int max_jobs, int ctl_slots, int ctas_per_sm, void *device_ws, size_t device_bytes,
-                     void *host_ws, size_t host_bytes, double run_seconds, csc_stream_t kernel_stream,
-                     csc_stream_t side_stream, csc_queue **out) {
+static int queue_launch(csc_queue *q) {
+    const size_t smem = 2 * (size_t)q->atoms.K * sizeof(float);
+    QueueCtl *qc = q->qc;
+    QueueJob *jobs = q->jobs;
+    QueueHostSlot *host = q->host;
+    int max_jobs = q->max_jobs;
+    unsigned long long run_ns = q->run_ns;
+    void *args[] = {&qc, &jobs, &max_jobs, &host, &run_ns};
+    const cudaError_t e = cudaLaunchKernel(q->kern, dim3(q->grid), dim3(kQueueThreads), args, smem, q->kstream);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    q->launched = true;
+    g_live_queues.fetch_add(1);
+    return CSC_OK;
+}
+
+static int queue_create(const csc_shape *atoms, const float *D, const float *dtd, const csc_solve_opts *opts,
+                        int max_jobs, int ctl_slots, int ctas_per_sm, void *device_ws, size_t device_bytes,
+                        void *host_ws, size_t host_bytes, double run_seconds, csc_stream_t kernel_stream,
+                        csc_stream_t side_stream, bool launch, csc_queue **out) {
     Geom g;
     int rc = atoms_geom(atoms, &g);
     if (rc) return rc;
@@ -336,23 +361,51 @@ int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, c
         return rc;
     }
     if ((e = cudaStreamSynchronize(ss)) != cudaSuccess) return fail(e);
-    const size_t smem = 2 * (size_t)g.K * sizeof(float);
-    QueueCtl *qc = q->qc;
-    QueueJob *jobs = q->jobs;
-    QueueHostSlot *host = q->host;
-    unsigned long long run_ns = (unsigned long long)(run_seconds * 1e9);
-    void *args[] = {&qc, &jobs, &max_jobs, &host, &run_ns};
-    if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(kQueueThreads), args, smem, q->kstream)) != cudaSuccess)
-        return fail(e);
+    q->kern = kern;
+    q->run_ns = (unsigned long long)(run_seconds * 1e9);
+    if (launch && (rc = queue_launch(q))) {
+        delete q;
+        return rc;
+    }
     *out = q;
-    g_live_queues.fetch_add(1);
     return CSC_OK;
+}
+
+int csc_queue_create(const csc_shape *atoms, const float *D, const float *dtd, const csc_solve_opts *opts,
+                     int max_jobs, int ctl_slots, int ctas_per_sm, void *device_ws, size_t device_bytes,
+                     void *host_ws, size_t host_bytes, double run_seconds, csc_stream_t kernel_stream,
+                     csc_stream_t side_stream, csc_queue **out) {
+    return queue_create(atoms, D, dtd, opts, max_jobs, ctl_slots, ctas_per_sm, device_ws, device_bytes, host_ws,
+                        host_bytes, run_seconds, kernel_stream, side_stream, true, out);
+}
+
+int csc_queue_create_deferred(const csc_shape *atoms, const float *D, const float *dtd,
+                              const csc_solve_opts *opts, int max_jobs, int ctl_slots, int ctas_per_sm,
+                              void *device_ws, size_t device_bytes, void *host_ws, size_t host_bytes,
+                              double run_seconds, csc_stream_t kernel_stream, csc_stream_t side_stream,
+                              csc_queue **out) {
+    return queue_create(atoms, D, dtd, opts, max_jobs, ctl_slots, ctas_per_sm, device_ws, device_bytes, host_ws,
+                        host_bytes, run_seconds, kernel_stream, side_stream, false, out);
+}
+
+int csc_queue_start(csc_queue *q, int drain) {
+    if (!q || q->launched || (drain != 0 && drain != 1)) return CSC_ERR_INVALID;
+    if (drain) {
+        // the drain word is set by a device-side memset (no host source) before the launch
+        cudaError_t e = cudaMemsetAsync(&q->qc->drain, 1, 1, q->sstream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(q->sstream);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        q->drain = true;
+    }
+    // the kernel stream follows everything the side stream published
+    return queue_launch(q);
 }
 
 int csc_queue_submit(csc_queue *q, int T0, int T1, float *beta, float *Z, float lambda, float tol, int warm_start,
                      const csc_solve_opts *opts, int *job_out) {
     if (!q || !beta || !Z || !job_out || !(lambda >= 0.f) || !(tol > 0.f)) return CSC_ERR_INVALID;
     if ((reinterpret_cast<uintptr_t>(beta) | reinterpret_cast<uintptr_t>(Z)) & 15) return CSC_ERR_INVALID;
+    if (q->drain) return CSC_ERR_INVALID;  // a draining kernel takes no job published after its start
     const csc_solve_opts o = opts ? *opts : q->opts;
     if (!(o.stop_margin >= 0.0 && o.stop_margin <= 1.0) || o.mode < 0 || o.mode > 2) return CSC_ERR_INVALID;
     if (q->njobs >= q->max_jobs || q->free_ctl.empty()) return CSC_ERR_WORKSPACE;
@@ -495,14 +548,21 @@ int csc_queue_inspect(csc_queue *q, int job, long long *out) {
 int csc_queue_close(csc_queue *q) {
     if (!q) return CSC_ERR_INVALID;
     int rc = CSC_OK;
-    // the close word is 0 since creation: setting its low byte makes it 1
-    // (a device-side write, no host source)
-    cudaError_t e = cudaMemsetAsync(&q->qc->close, 1, 1, q->sstream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(q->sstream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(q->kstream);
+    cudaError_t e = cudaSuccess;
+    if (q->launched) {
+        // a draining kernel ends by itself once its jobs are done
+        if (q->drain) e = cudaStreamSynchronize(q->kstream);
+        // the close word is 0 since creation: setting its low byte makes it 1
+        // (a device-side write, no host source)
+        if (e == cudaSuccess) e = cudaMemsetAsync(&q->qc->close, 1, 1, q->sstream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(q->sstream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(q->kstream);
+        g_live_queues.fetch_sub(1);
+    } else {
+        e = cudaStreamSynchronize(q->sstream);  // submits of a queue never started
+    }
     if (e != cudaSuccess) rc = set_cuda_error(e);
     delete q;
-    g_live_queues.fetch_sub(1);
     return rc;
 }
 

@@ -215,3 +215,54 @@ def test_dropped_queue_stops_its_kernel(pkg):
     t0 = time.monotonic()
     ks.synchronize()  # returns by run_seconds at the latest
     assert time.monotonic() - t0 < 5.0
+
+
+def test_deferred_queue_drains_jobs_published_before_its_start(pkg, orc):
+    """Jobs submitted to a queue made with start=False are all published
+    before its kernel runs; start(drain=True) lets the kernel end by itself
+    once they are done, so no host copy overlaps the kernel.  Results match
+    the oracle; a submit after a draining start is refused."""
+    import torch
+    D = _atoms(9)
+    Dd = dev(D)
+    imgs = [_image(48, 40, 21, D), _image(33, 61, 22, D), _image(70, 70, 23, D)]
+    reqs = [_Req(pkg, X, Dd) for X in imgs]
+    rounds = [0] * len(reqs)
+    pending = list(range(len(reqs)))
+    warm = False
+    while pending:
+        q = pkg.Queue(Dd, reqs[0].dtd, max_jobs=16, ctl_slots=8, run_seconds=60.0, start=False)
+        jobs = {i: q.submit(reqs[i].beta, reqs[i].Z, reqs[i].lam, TOL, warm_start=warm) for i in pending}
+        q.start(drain=True)
+        with pytest.raises(pkg.CscError) as e:
+            q.submit(reqs[0].beta, reqs[0].Z, reqs[0].lam, TOL)
+        assert e.value.status == pkg.CSC_ERR_INVALID
+        stats = {i: q.wait(j) for i, j in jobs.items()}
+        q.close()
+        nxt = []
+        for i in pending:
+            assert stats[i]["status"] == 0, stats[i]
+            r = reqs[i]
+            _, mdz, _ = pkg.csc_refresh_beta(r.X, Dd, r.Z, r.lam, beta=r.beta, ws=r.ws)
+            rounds[i] += 1
+            if mdz >= TOL:
+                assert rounds[i] < 4, (i, mdz)
+                nxt.append(i)
+        pending, warm = nxt, True
+    torch.cuda.synchronize()
+    for X, r in zip(imgs, reqs):
+        ref = orc.lgcd(X, D, r.lam, TOL)
+        f_ref = orc.objective(X, D, ref["Z"], r.lam)
+        f = orc.objective(X, D, host(r.Z), r.lam)
+        assert abs(f - f_ref) <= REL * abs(f_ref), (f, f_ref)
+
+
+def test_deferred_queue_closed_without_start(pkg):
+    D = _atoms(9)
+    Dd = dev(D)
+    r = _Req(pkg, _image(40, 40, 24, D), Dd)
+    q = pkg.Queue(Dd, r.dtd, max_jobs=4, ctl_slots=2, run_seconds=10.0, start=False)
+    q.submit(r.beta, r.Z, r.lam, TOL)
+    q.close()  # the kernel never ran; the handle is released
+    with pytest.raises(RuntimeError):
+        q.submit(r.beta, r.Z, r.lam, TOL)
