@@ -91,7 +91,8 @@ typedef struct {
                              memory (used when a tile's beta, Z and table do not fit)      */
     int beta_init;        /* cdl_fit: 0 = beta-init in FP32 (csc_init_beta), 1 = on the
                              tensor cores in split bf16 (csc_init_beta_bf16x3) after the
-                             first iteration, whose exact beta also fixes lambda          */
+                             first iteration, whose exact beta also fixes lambda; cdl_step:
+                             the same choice when lambda is given                       */
     double stop_margin;   /* workers stop when no |dZ| reaches stop_margin * tol, in (0, 1]
                              (0 = 0.99 in FP32, 1 in FP64); the check on a beta
                              recomputed from scratch always uses tol itself            */
@@ -218,29 +219,35 @@ CSC_API int cdl_fit(const csc_shape *shape, const float *X, float *D, float *Z, 
                     size_t workspace_bytes, double *trace, int *n_outer, csc_stream_t stream);
 
 /* One pass of the loop body of Alg. 2 as a single call:
- *   beta, dtd, lambda_max <- csc_init_beta(X, D);  lambda = reg * lambda_max
- *   (of this D, rounded to float as csc_lgcd_solve receives it);
+ *   beta, dtd <- csc_init_beta(X, D) (csc_init_beta_bf16x3 when lambda is
+ *        given and opts->beta_init = 1);
+ *   lambda: the given one when lambda > 0 (reg is then ignored), so that the
+ *        calls of an outer loop solve one fixed problem; otherwise
+ *        reg * lambda_max(X, D) from the FP32 beta-init (rounded to float as
+ *        csc_lgcd_solve receives it);
  *   Z <- csc_lgcd_solve(X, D, lambda, tol, opts) (from Z = 0 unless
  *        opts->warm_start);
  *   phi, psi <- cdl_dict_stats(Z, X);
  *   D <- cdl_dict_update(phi, psi, x_sqnorm) (pgd_max_iter, pgd_tol).
- * Same buffers, layouts and results as those four calls; between the
- * statistics and the dictionary step nothing waits for the device (the
- * nonzero count is read back once, with the dictionary step's results).
- *   D: in / out.  Z, beta, dtd, phi, psi: outputs.  x_sqnorm: ||X||_2^2.
- *   stats: the solve's statistics (may be NULL).  lambda_out, dict_cost_out
- *   (F(D) after the step, as cdl_dict_update's objective_out) and
- *   dict_iters_out: host pointers (may be NULL).
- * Synchronises `stream` three times (lambda_max, the end of the solve, the
- * end of the step).  Returns the solve's status (CSC_OK or CSC_NOT_CONVERGED;
- * the dictionary step still ran), CSC_ERR_WORKSPACE when Z has more nonzeros
- * than the workspace's list holds (phi, psi and D are then not valid), or the
- * first error of a stage. */
+ * Same buffers, layouts and results as those calls; between the statistics
+ * and the dictionary step nothing waits for the device (the nonzero count is
+ * read back once, with the dictionary step's results).
+ *   D: in / out.  Z, beta, dtd, phi, psi: outputs.  x_sqnorm: ||X||_2^2, or a
+ *   negative value to have it summed on the device (FP64).
+ *   stats: the solve's statistics (may be NULL).  lambda_out (the lambda
+ *   used), dict_cost_out (F(D) after the step, as cdl_dict_update's
+ *   objective_out) and dict_iters_out: host pointers (may be NULL).
+ * Synchronises `stream` two or three times (lambda_max when it is computed,
+ * the end of the solve, the end of the step).  Returns the solve's status
+ * (CSC_OK or CSC_NOT_CONVERGED; the dictionary step still ran),
+ * CSC_ERR_INVALID for neither lambda > 0 nor reg > 0, CSC_ERR_WORKSPACE when
+ * Z has more nonzeros than the workspace's list holds (phi and psi are then
+ * not valid and D is left unchanged), or the first error of a stage. */
 CSC_API int cdl_step(const csc_shape *shape, const float *X, float *D, float *Z, float *beta, float *dtd,
-                     float *phi, float *psi, double reg, double tol, double x_sqnorm, int pgd_max_iter,
-                     double pgd_tol, const csc_solve_opts *opts, void *workspace, size_t workspace_bytes,
-                     csc_solve_stats *stats, double *lambda_out, double *dict_cost_out,
-                     int *dict_iters_out, csc_stream_t stream);
+                     float *phi, float *psi, double reg, double lambda, double tol, double x_sqnorm,
+                     int pgd_max_iter, double pgd_tol, const csc_solve_opts *opts, void *workspace,
+                     size_t workspace_bytes, csc_solve_stats *stats, double *lambda_out,
+                     double *dict_cost_out, int *dict_iters_out, csc_stream_t stream);
 
 /* csc_init_beta with the correlation on the tensor cores (tcgen05) in
  * split-bf16 precision: each X and D value is split into bf16 hi + lo parts
@@ -392,9 +399,12 @@ CSC_API int csc_lgcd_solve_f64(const csc_shape *shape, const double *X, const do
  *   The call allocates nothing (no cudaMalloc/cudaFree, no allocating library
  *   routine).
  *   Returns CSC_ERR_WORKSPACE when the problem needs more scratch than the
- *   array holds (the nonzero list of Z plus the FP64 accumulators of phi and
- *   psi; the 1-D P=5, T=200,000, K=10, L=64 problem needs about 1.7 MB).
- *   The first call on a device looks up the array's device address; make that
+ *   array holds: the FP64 accumulators of phi and psi and a control block
+ *   take their share, and the rest of the array holds the nonzero list of Z
+ *   (12 bytes per nonzero, about 690,000 nonzeros for small atoms); a Z with
+ *   more nonzeros than that is refused after the count.
+ *   The first call on a device (and the first after that device's context
+ *   was reset or created anew) looks up the array's device address; make that
  *   first call before any stream capture.  All calls share the one array:
  *   calls whose work overlaps on the GPU (different streams, different host
  *   threads) race and must be serialised by the caller.  Like cdl_dict_stats,

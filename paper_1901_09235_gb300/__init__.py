@@ -100,7 +100,7 @@ def load():
         "cdl_dict_stats": (i, [S, p, p, p, p, p, sz, p]),
         "cdl_dict_update": (i, [S, p, p, d, p, i, d, C.POINTER(d), C.POINTER(i), p, sz, p]),
         "cdl_fit": (i, [S, p, p, p, p, p, p, p, d, d, i, d, i, d, O, p, sz, C.POINTER(d), C.POINTER(i), p]),
-        "cdl_step": (i, [S, p, p, p, p, p, p, p, d, d, d, i, d, O, p, sz, ST, C.POINTER(d), C.POINTER(d),
+        "cdl_step": (i, [S, p, p, p, p, p, p, p, d, d, d, d, i, d, O, p, sz, ST, C.POINTER(d), C.POINTER(d),
                          C.POINTER(i), p]),
         "csc_refresh_beta": (i, [S, p, p, p, C.c_float, p, C.POINTER(d), C.POINTER(d), p, sz, p]),
         "csc_rcd_solve": (i, [S, p, p, p, p, C.c_float, p, C.c_longlong, C.POINTER(C.c_longlong), p, sz, p]),
@@ -522,27 +522,29 @@ def cdl_fit(X, D, reg: float = 0.1, tol: float = 1e-4, max_outer: int = 10, nu: 
 
 
 def cdl_step(X, D, prob, reg: float = 0.1, tol: float = 1e-4, x_sqnorm: float | None = None,
-             pgd_max_iter: int = 50, pgd_tol: float = 1e-8, opts: SolveOpts | None = None, stream=None):
+             pgd_max_iter: int = 50, pgd_tol: float = 1e-8, opts: SolveOpts | None = None, stream=None,
+             lam: float | None = None):
     """One pass of the loop body of Alg. 2 in one call (cdl_step): beta-init,
-    LGCD with lambda = reg * lambda_max(X, D), phi / psi and the dictionary
-    step, into the buffers of ``prob`` (a Problem of the same shapes); D is
-    updated in place.  Returns (Z, stats): the solve statistics plus
-    'lambda', 'dict_F' and 'dict_iters'."""
+    LGCD with the given lambda (``lam``) or lambda = reg * lambda_max(X, D),
+    phi / psi and the dictionary step, into the buffers of ``prob`` (a
+    Problem of the same shapes); D is updated in place.  x_sqnorm None: summed
+    on the device.  Returns (Z, stats): the solve statistics plus 'lambda',
+    'dict_F' and 'dict_iters'."""
     import torch
     _need(X, torch.float32, "X")
     _need(D, torch.float32, "D")
     s = prob.shape
-    if x_sqnorm is None:
-        x_sqnorm = float((X.double() ** 2).sum())
     st = SolveStats()
-    lam, fd, it = C.c_double(0.0), C.c_double(0.0), C.c_int(0)
+    lam_out, fd, it = C.c_double(0.0), C.c_double(0.0), C.c_int(0)
     rc = load().cdl_step(C.byref(s), _ptr(X), _ptr(D), _ptr(prob.Z), _ptr(prob.beta), _ptr(prob.dtd),
-                         _ptr(prob.phi), _ptr(prob.psi), float(reg), float(tol), float(x_sqnorm),
+                         _ptr(prob.phi), _ptr(prob.psi), float(reg), float(lam or 0.0), float(tol),
+                         -1.0 if x_sqnorm is None else float(x_sqnorm),
                          int(pgd_max_iter), float(pgd_tol), C.byref(opts) if opts else None, _ptr(prob.ws),
-                         prob.ws.numel(), C.byref(st), C.byref(lam), C.byref(fd), C.byref(it), _stream(stream))
+                         prob.ws.numel(), C.byref(st), C.byref(lam_out), C.byref(fd), C.byref(it),
+                         _stream(stream))
     stats = st.as_dict()
     _check(rc, "cdl_step", soft=(CSC_NOT_CONVERGED,), stats=stats)
-    stats["lambda"], stats["dict_F"], stats["dict_iters"] = lam.value, fd.value, it.value
+    stats["lambda"], stats["dict_F"], stats["dict_iters"] = lam_out.value, fd.value, it.value
     return prob.Z, stats
 
 

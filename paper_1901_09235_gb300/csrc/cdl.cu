@@ -103,34 +103,61 @@ extern "C" int cdl_fit(const csc_shape *shape, const float *X, float *D, float *
 }
 
 extern "C" int cdl_step(const csc_shape *shape, const float *X, float *D, float *Z, float *beta, float *dtd,
-                        float *phi, float *psi, double reg, double tol, double x_sqnorm, int pgd_max_iter,
-                        double pgd_tol, const csc_solve_opts *opts, void *ws, size_t ws_bytes,
+                        float *phi, float *psi, double reg, double lambda, double tol, double x_sqnorm,
+                        int pgd_max_iter, double pgd_tol, const csc_solve_opts *opts, void *ws, size_t ws_bytes,
                         csc_solve_stats *stats, double *lambda_out, double *dict_cost_out, int *dict_iters_out,
                         csc_stream_t stream) {
     Geom g;
     int rc = make_geom(shape, &g);
     if (rc) return rc;
     if (!X || !D || !Z || !beta || !dtd || !phi || !psi || !ws) return CSC_ERR_INVALID;
-    if (!(reg > 0.0) || !(tol > 0.0) || !(x_sqnorm >= 0.0) || pgd_max_iter < 0 || !(pgd_tol >= 0.0))
+    if (!(lambda > 0.0) && !(reg > 0.0)) return CSC_ERR_INVALID;
+    if (!(tol > 0.0) || std::isnan(x_sqnorm) || pgd_max_iter < 0 || !(pgd_tol >= 0.0) || std::isnan(lambda))
         return CSC_ERR_INVALID;
+    csc_solve_opts o;
+    csc_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.beta_init < 0 || o.beta_init > 1) return CSC_ERR_INVALID;
     WsLayout L = plan_workspace(g, 0, 4);
     if (ws_bytes < L.total) return CSC_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *wsb = static_cast<unsigned char *>(ws);
     WsHeader *h = reinterpret_cast<WsHeader *>(wsb + L.hdr);
 
-    // beta, the D^T D table and lambda_max; lambda = reg * lambda_max of this D
-    double lmax = 0.0;
-    if ((rc = csc_init_beta(shape, X, D, beta, dtd, &lmax, ws, ws_bytes, stream))) return rc;
-    const float lambda = (float)(reg * lmax);
-    if (lambda_out) *lambda_out = lambda;
+    // ||X||^2 on the device when the caller does not give it; the dictionary
+    // step reads it there (no synchronisation)
+    const double *xsq_dev = nullptr;
+    if (x_sqnorm < 0.0) {
+        CSC_CUDA(cudaMemsetAsync(&h->xsq, 0, sizeof(double), st));
+        sumsq_kernel<256><<<1216, 256, 0, st>>>(X, g.nx(), &h->xsq);
+        CSC_CUDA(cudaGetLastError());
+        xsq_dev = &h->xsq;
+    }
+    // beta and the D^T D table.  A given lambda (> 0) is used as it is, so that
+    // the calls of an outer loop solve one fixed problem (Alg. 2); otherwise
+    // lambda = reg * lambda_max of this D, from the FP32 beta-init.  With a
+    // given lambda, opts->beta_init = 1 runs the beta-init on the tensor cores.
+    float lam;
+    if (lambda > 0.0) {
+        lam = (float)lambda;
+        rc = o.beta_init == 1 ? csc_init_beta_bf16x3(shape, X, D, beta, dtd, nullptr, ws, ws_bytes, stream)
+                              : csc_init_beta(shape, X, D, beta, dtd, nullptr, ws, ws_bytes, stream);
+        if (rc) return rc;
+    } else {
+        double lmax = 0.0;
+        if ((rc = csc_init_beta(shape, X, D, beta, dtd, &lmax, ws, ws_bytes, stream))) return rc;
+        lam = (float)(reg * lmax);
+    }
+    if (lambda_out) *lambda_out = lam;
     // Z by LGCD with soft-locks (Alg. 3)
-    const int solve_rc = csc_lgcd_solve(shape, X, D, dtd, beta, Z, lambda, (float)tol, opts, ws, ws_bytes,
-                                        stats, stream);
+    const int solve_rc = csc_lgcd_solve(shape, X, D, dtd, beta, Z, lam, (float)tol, &o, ws, ws_bytes, stats,
+                                        stream);
     if (solve_rc != CSC_OK && solve_rc != CSC_NOT_CONVERGED) return solve_rc;
-    // phi, psi and the dictionary step, queued without a synchronisation in between
+    // phi, psi and the dictionary step, queued without a synchronisation in
+    // between; a nonzero list that overflowed leaves D unchanged
     if ((rc = dict_stats_deferred(g, Z, X, phi, psi, wsb, L, st))) return rc;
-    if ((rc = dict_update_impl(g, phi, psi, x_sqnorm, D, pgd_max_iter, pgd_tol, nullptr, nullptr, wsb, L, st)))
+    if ((rc = dict_update_impl(g, phi, psi, x_sqnorm, D, pgd_max_iter, pgd_tol, nullptr, nullptr, wsb, L, st,
+                               xsq_dev, &h->scan_total, (int)L.nnz_cap)))
         return rc;
     // one read-back: the dictionary step's results and the nonzero count
     struct Tail {

@@ -61,7 +61,9 @@ struct alignas(128) WsHeader {
     double obj_g;           // sum |Z|
     double pgd_out[12];     // dictionary step: objective, iterations, last step, spare, phase cycles [4..9]
     int scan_total;         // deterministic compaction: total count
-    int pad6[15];
+    int pad6a;
+    double xsq;             // ||X||^2 when a call computes it on the device
+    int pad6[12];
     unsigned long long tphmax[8];      // largest per-worker SM cycles per phase
 };
 
@@ -282,8 +284,12 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
 
 int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, float *psi,
                     unsigned char *ws, const WsLayout &L, cudaStream_t st);
+// x_sqnorm_dev (optional): ||X||^2 in device memory, read by the kernel in
+// place of x_sqnorm.  gate (optional): when *gate > gate_cap at run time the
+// step leaves D unchanged (statistics that were not computed).
 int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x_sqnorm, float *D,
                      int max_iter, double tol, double *obj_out, int *it_out, unsigned char *ws,
-                     const WsLayout &L, cudaStream_t st);
+                     const WsLayout &L, cudaStream_t st, const double *x_sqnorm_dev = nullptr,
+                     const int *gate = nullptr, int gate_cap = 0);
 
 }  // namespace csc

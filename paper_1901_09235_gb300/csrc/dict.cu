@@ -293,6 +293,9 @@ struct PgdArgs {
     float *qd, *qg;  // per-CTA scratch: [cluster rank][K sources][ka * per]
     double *out;   // [objective, iterations, eta, Armijo trials, phase cycles x 6]
     double x_sqnorm, tol;
+    const double *x_sqnorm_dev;  // when set, ||X||^2 is read here instead of x_sqnorm
+    const int *gate;             // when set and *gate > gate_cap, D is left unchanged
+    int gate_cap;
     int K, P, L0, L1, max_iter, ka, stage_phi, q_in_smem;
 };
 
@@ -422,6 +425,15 @@ __device__ __forceinline__ void conv_per_source(const PgdArgs &a, const float *s
 }
 
 __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
+    // statistics that were not computed (their nonzero list overflowed): every
+    // CTA of the cluster returns before any barrier, D is left as it is
+    if (a.gate && *a.gate > a.gate_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.out[0] = 0.0;
+            a.out[1] = 0.0;
+        }
+        return;
+    }
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K = a.K, LL = a.L0 * a.L1, per = a.P * LL, n = K * per;
@@ -689,7 +701,7 @@ __global__ void __launch_bounds__(kPgdThreads, 1) pgd_kernel(PgdArgs a) {
             tp += cl.map_shared_rank(fin, (unsigned)r)[0];
             tg += cl.map_shared_rank(fin, (unsigned)r)[1];
         }
-        a.out[0] = 0.5 * a.x_sqnorm - 0.5 * tp + 0.5 * tg;
+        a.out[0] = 0.5 * (a.x_sqnorm_dev ? *a.x_sqnorm_dev : a.x_sqnorm) - 0.5 * tp + 0.5 * tg;
         a.out[1] = (double)it;
         a.out[2] = eta;
         a.out[3] = (double)n_trials;
@@ -710,7 +722,8 @@ static size_t pgd_smem(const Geom &g, int ka, bool stage, bool qsm) {
 
 int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x_sqnorm, float *D,
                      int max_iter, double tol, double *obj_out, int *it_out, unsigned char *ws,
-                     const WsLayout &L, cudaStream_t st) {
+                     const WsLayout &L, cudaStream_t st, const double *x_sqnorm_dev, const int *gate,
+                     int gate_cap) {
     if (g.K > kPgdMaxK) return CSC_ERR_UNIMPLEMENTED;
     WsHeader *h = reinterpret_cast<WsHeader *>(ws + L.hdr);
     PgdArgs a;
@@ -721,6 +734,9 @@ int dict_update_impl(const Geom &g, const float *phi, const float *psi, double x
     a.qg = a.qd + (size_t)g.K * g.nd() + 16 * (size_t)g.natom() * g.K;
     a.out = h->pgd_out;
     a.x_sqnorm = x_sqnorm;
+    a.x_sqnorm_dev = x_sqnorm_dev;
+    a.gate = gate;
+    a.gate_cap = gate_cap;
     a.tol = tol;
     a.K = g.K;
     a.P = g.P;

@@ -117,19 +117,20 @@ def test_option_and_queue_arguments_rejected_on_host(lib):
 
 
 def test_cdl_step_arguments_rejected_on_host(lib):
-    """The fused loop-body call refuses missing buffers, non-positive reg or
-    tol, a negative ||X||^2 and a short workspace before any device work (the
-    pointers below are never dereferenced)."""
+    """The fused loop-body call refuses missing buffers, neither a positive
+    lambda nor a positive reg, a non-positive tol, a NaN ||X||^2 and a short
+    workspace before any device work (the pointers below are never
+    dereferenced)."""
     import paper_1901_09235_gb300 as pkg
     s = pkg.make_shape((2, 100), (3, 2, 5))
     st = pkg.SolveStats()
     fake = [C.c_void_p(16 * (i + 1)) for i in range(8)]
     need = pkg.workspace_size(s)
 
-    def call(ptrs=fake[:7], reg=0.1, tol=1e-4, xs=1.0, ws=fake[7], ws_bytes=need):
-        lam, fd, it = C.c_double(0), C.c_double(0), C.c_int(0)
-        return lib.cdl_step(C.byref(s), *ptrs, reg, tol, xs, 50, 1e-8, None, ws, ws_bytes, C.byref(st),
-                            C.byref(lam), C.byref(fd), C.byref(it), None)
+    def call(ptrs=fake[:7], reg=0.1, lam=0.0, tol=1e-4, xs=1.0, ws=fake[7], ws_bytes=need):
+        lo, fd, it = C.c_double(0), C.c_double(0), C.c_int(0)
+        return lib.cdl_step(C.byref(s), *ptrs, reg, lam, tol, xs, 50, 1e-8, None, ws, ws_bytes, C.byref(st),
+                            C.byref(lo), C.byref(fd), C.byref(it), None)
 
     for i in range(7):
         ptrs = list(fake[:7])
@@ -138,6 +139,11 @@ def test_cdl_step_arguments_rejected_on_host(lib):
     assert call(ws=None) == pkg.CSC_ERR_INVALID
     for reg in (0.0, -1.0, float("nan")):
         assert call(reg=reg) == pkg.CSC_ERR_INVALID
+        assert call(reg=reg, lam=float("nan")) == pkg.CSC_ERR_INVALID
     assert call(tol=0.0) == pkg.CSC_ERR_INVALID
-    assert call(xs=-1.0) == pkg.CSC_ERR_INVALID
+    assert call(xs=float("nan")) == pkg.CSC_ERR_INVALID
+    bad_opts = pkg.default_opts(beta_init=2)
+    lo, fd, it = C.c_double(0), C.c_double(0), C.c_int(0)
+    assert lib.cdl_step(C.byref(s), *fake[:7], 0.1, 0.0, 1e-4, 1.0, 50, 1e-8, C.byref(bad_opts), fake[7], need,
+                        C.byref(st), C.byref(lo), C.byref(fd), C.byref(it), None) == pkg.CSC_ERR_INVALID
     assert call(ws_bytes=1024) == pkg.CSC_ERR_WORKSPACE

@@ -145,6 +145,38 @@ def test_cdl_step_matches_the_separate_calls(pkg, orc, w):
     assert F2 == st["dict_F"] and it2 == st["dict_iters"]
 
 
+def test_chained_cdl_steps_with_a_fixed_lambda_follow_cdl_fit(pkg, orc):
+    """Two cdl_step calls, the second with the first one's lambda, solve the
+    fixed problem of Alg. 2 as cdl_fit's first two iterations do: the costs
+    after each CSC step agree (the solves are asynchronous, so within the
+    solve tolerance, not bit for bit) and so do the dictionaries.  ||X||^2 is
+    summed on the device; beta-init in FP32 and, for the second call, on the
+    tensor cores."""
+    w = Workload("chain96", P=1, K=4, T=(96, 96), L=(8, 8), density=5e-3, sigma=0.05, nonneg=True)
+    X, D0, _ = make_problem(w, 41)
+    rng = np.random.default_rng(5)
+    D0 = D0 + 0.3 * rng.standard_normal(D0.shape).astype(np.float32)
+    D0 /= np.sqrt((D0.reshape(w.K, -1) ** 2).sum(1)).reshape(-1, 1, 1, 1)
+    Xd = dev(X)
+    Dfit = dev(D0)
+    _, tr, rc = pkg.cdl_fit(Xd, Dfit, reg=0.1, tol=1e-4, max_outer=2, nu=0.0, pgd_max_iter=20)
+    assert rc == 0 and len(tr) == 2
+    for beta_init in (0, 1):
+        D = dev(D0)
+        prob = pkg.Problem.create(Xd, D)
+        _, s1 = pkg.cdl_step(Xd, D, prob, reg=0.1, tol=1e-4, pgd_max_iter=20)
+        lam = s1["lambda"]
+        _, s2 = pkg.cdl_step(Xd, D, prob, reg=0.0, lam=lam, tol=1e-4, pgd_max_iter=20,
+                             opts=pkg.default_opts(beta_init=beta_init))
+        assert s1["status"] == 0 and s2["status"] == 0 and s2["lambda"] == lam
+        for st, (c_csc, _) in zip((s1, s2), tr):
+            assert abs(st["objective"] - c_csc) <= 1e-5 * abs(c_csc), (st["objective"], c_csc)
+        assert np.allclose(host(D), host(Dfit), rtol=0, atol=1e-3)
+        # the same cost on the oracle's side: its loop with the same fixed lambda
+        _, _, tr_ref = orc.cdl(X, D0, 0.1, 1e-4, 2, pgd_max_iter=20)
+        assert abs(s2["objective"] - tr_ref[1][0]) <= 1e-4 * abs(tr_ref[1][0])
+
+
 def test_cdl_step_reports_a_nonzero_list_overflow(pkg):
     """A Z with more nonzeros than the workspace's list holds: cdl_step, which
     reads the count back only at the end, still answers CSC_ERR_WORKSPACE
@@ -158,9 +190,12 @@ def test_cdl_step_reports_a_nonzero_list_overflow(pkg):
     gen = torch.Generator(device="cuda").manual_seed(3)
     prob.Z.copy_(0.01 * (torch.rand(prob.Z.shape, generator=gen, device="cuda") + 0.5))
     opts = pkg.default_opts(warm_start=1, max_updates=1)
+    D_before = D.clone()
     with pytest.raises(pkg.CscError) as e:
         pkg.cdl_step(Xd, D, prob, reg=0.1, tol=1e-4, opts=opts)
     assert e.value.status == pkg.CSC_ERR_WORKSPACE
+    # the dictionary step did not run on the statistics that were not computed
+    assert torch.equal(D, D_before)
     # the separate statistics call reports the same overflow
     with pytest.raises(pkg.CscError) as e2:
         pkg.cdl_dict_stats(prob.Z, Xd, tuple(D0.shape), prob.phi, prob.psi, prob.ws)

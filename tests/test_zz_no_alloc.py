@@ -72,3 +72,23 @@ def test_noalloc_rejects_problems_beyond_its_scratch(pkg):
     p = C.c_void_p(dummy.data_ptr())
     rc = pkg.load().cdl_dict_stats_noalloc(C.byref(s), p, p, p, p, None)
     assert rc == pkg.CSC_ERR_WORKSPACE
+
+
+def test_noalloc_holds_more_nonzeros_than_the_workspace_list(pkg, orc):
+    """The nonzero list takes whatever the fixed array leaves after the
+    accumulators: a Z with more nonzeros than the workspace form's list
+    (max(2^16, K |Omega| / 16) entries) still fits, and phi / psi match the
+    FP64 oracle within the bounds of their FP32 and FP64 sums."""
+    import torch
+    from tests._gpu import gamma
+    w = Workload("na_dense", P=1, K=4, T=(300_000,), L=(16,), density=0.08, sigma=0.1)
+    X, D, Z = make_problem(w, 34)
+    nnz = int((Z != 0).sum())
+    nz = Z.size
+    assert nnz > max(1 << 16, nz // 16) and nnz * 12 < (7 << 20)
+    Xd, Zd = torch.from_numpy(X).cuda(), torch.from_numpy(Z).cuda()
+    phi, psi = _noalloc(pkg, Zd, Xd, D.shape)
+    pr, sr = orc.phi_psi(Z, X, w.L)
+    pa, sa = orc.phi_psi(np.abs(Z), np.abs(X), w.L)
+    assert np.all(np.abs(phi - pr) <= 2.0 ** -24 * np.abs(pr) + 1e-12 * pa)
+    assert np.all(np.abs(psi - sr) <= gamma(65) * sa + 1e-12 * np.abs(sr).max())
