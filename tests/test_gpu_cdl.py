@@ -200,3 +200,37 @@ def test_cdl_step_reports_a_nonzero_list_overflow(pkg):
     with pytest.raises(pkg.CscError) as e2:
         pkg.cdl_dict_stats(prob.Z, Xd, tuple(D0.shape), prob.phi, prob.psi, prob.ws)
     assert e2.value.status == pkg.CSC_ERR_WORKSPACE
+
+
+_CROP = {}
+
+
+def _crop_8192_family_oracle(orc):
+    """A 1024 x 1024 image of the 8192^2 workload's family (same generator,
+    25 atoms of 32 x 32, density 5e-5, noise 0.05) and the oracle's loop on it
+    (Alg. 2 from the generating atoms, three outer iterations, five PGD
+    iterations each), computed once for both precisions."""
+    if not _CROP:
+        from synthetic import scaled
+        w = scaled(IMAGE_8192, (1024, 1024))
+        X, D0, _ = make_problem(w, 5)
+        _, _, tr = orc.cdl(X, D0, w.reg, w.tol, 3, pgd_max_iter=5)
+        _CROP.update(w=w, X=X, D0=D0, trace=tr)
+    return _CROP
+
+
+@pytest.mark.parametrize("beta_init", [0, 1], ids=["fp32", "bf16x3"])
+def test_cdl_1024_crop_of_the_8192_family_against_the_oracle_loop(pkg, orc, beta_init):
+    """cdl_fit on the crop in the bench's precisions (FP32 beta-init, or split
+    bf16 after the first iteration) against the oracle's loop: the cost after
+    every CSC step and after every dictionary step within 1e-4 relative."""
+    c = _crop_8192_family_oracle(orc)
+    w = c["w"]
+    Dd = dev(c["D0"])
+    _, tr, rc = pkg.cdl_fit(dev(c["X"]), Dd, reg=w.reg, tol=w.tol, max_outer=3, nu=0.0, pgd_max_iter=5,
+                            opts=pkg.default_opts(beta_init=beta_init))
+    assert rc == 0 and len(tr) == 3
+    for (a, b), (ra, rb) in zip(tr, c["trace"]):
+        assert abs(a - ra) <= 1e-4 * abs(ra), (a, ra)
+        assert abs(b - rb) <= 1e-4 * abs(rb), (b, rb)
+    _monotone(tr)
