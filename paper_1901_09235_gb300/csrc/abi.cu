@@ -91,7 +91,27 @@ WsLayout plan_workspace(const Geom &g, int max_workers, int rs) {
     // solve, from which the global-tile solve rebuilds beta for its final
     // KKT test (a workspace that ends at `total` takes the correlation)
     L.beta0 = off;
-    L.total_beta0 = rs == 4 ? align256(off + (size_t)g.nz() * rs) : off;
+    if (rs == 4) {
+        size_t o2 = align256(off + (size_t)g.nz() * rs);
+        // gather of the rebuilt beta: bins of gbh x gbw positions (one output
+        // tile of its kernel each), their offsets and fill cursors, the binned
+        // list (16 bytes per nonzero) and C transposed to [k2][delta][k]
+        L.gbh = g.d == 1 ? 1 : 8;
+        L.gbw = g.d == 1 ? 512 : 64;
+        L.gnb0 = (int)ceil_div(g.Z0, L.gbh);
+        L.gnb1 = (int)ceil_div(g.Z1, L.gbw);
+        L.gkp = (g.K + 3) / 4 * 4;
+        const size_t nbins = (size_t)L.gnb0 * L.gnb1;
+        L.gbin = o2;
+        o2 = align256(o2 + 2 * (nbins + 1) * sizeof(int));
+        L.glist = o2;
+        o2 = align256(o2 + (size_t)L.nnz_cap * 16);
+        L.gtab = o2;
+        o2 = align256(o2 + (size_t)g.K * g.W0 * g.W1 * L.gkp * sizeof(float));
+        L.total_beta0 = o2;
+    } else {
+        L.total_beta0 = off;
+    }
     return L;
 }
 

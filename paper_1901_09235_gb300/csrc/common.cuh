@@ -75,6 +75,10 @@ constexpr int kDirs = 8;            // neighbour directions in a 2-D tile grid
 struct WsLayout {
     size_t hdr, nrm, dmax, nnz_k, nnz_s, nnz_z, blk, r64, rr, phi64, psi64, pgd, mbox_slots,
         mbox_ctl, total, beta0, total_beta0;  // beta0: optional region up to total_beta0
+    // inside the optional region, after beta0: the rebuilt-beta gather's bin
+    // offsets and cursors, its binned nonzero list and the transposed table
+    size_t gbin, glist, gtab;
+    int gbh, gbw, gnb0, gnb1, gkp;  // bin rows / columns, bins per dimension, padded K
     long long nnz_cap;
     int max_workers;
     int blk_cap;

@@ -201,6 +201,176 @@ __global__ void __launch_bounds__(NT) maxdz_kernel(const float *beta, const floa
     block_max_atomic<NT>(m, bits);
 }
 
+// ---------------------------------- the rebuilt beta as a gather (K <= 32)
+// The same beta = beta0 - sum C[k][k'][s - s'] z' over the nonzeros, without
+// reductions: the nonzeros are sorted into bins of gbh x gbw positions (a
+// count, a prefix sum, a fill), then one thread per output position sums the
+// terms of the nonzeros whose window holds it -- the CTA of an output tile
+// stages the nonzeros of the bins within L_i - 1 of the tile in shared
+// memory -- for every atom at once, writes beta and takes max |dZ| on it.
+// The table is read transposed, C_t[k'][delta][k] (K padded to a multiple of
+// four), so that the K coefficients of one term are contiguous (measured:
+// 5.7 ms against 8.2 ms reading C as stored on the 4096^2 image).
+struct GatherArgs {
+    const float *beta0, *Z, *ct;  // ct: C_t
+    float *beta;
+    const int *off;    // [nbins + 1] bin offsets into the list
+    const int4 *list;  // (k, row, column, z bits) by bin
+    const double *nrm;
+    const WsHeader *h;
+    unsigned long long *bits;
+    float lambda;
+    int K, Kp, Z0, Z1, L0, L1, W0, W1, bh, bw, nb0, nb1;
+};
+
+constexpr int kGatherStage = 1024;  // staged nonzeros per pass (16 KB)
+
+__global__ void ctab_kernel(const float *dtd, float *ct, int K, int Kp, int W) {
+    const long long n = (long long)K * W * Kp;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(q % Kp);
+        const long long r = q / Kp;  // k2 * W + delta
+        const int k2 = (int)(r / W), d = (int)(r % W);
+        ct[q] = k < K ? dtd[((size_t)k * K + k2) * W + d] : 0.f;
+    }
+}
+
+__global__ void bin_count_kernel(const int *ns, const WsHeader *h, long long cap, int *cnt, int Z1, int bh, int bw,
+                                 int nb1) {
+    if (h->overflow) return;
+    const long long n = h->nnz < cap ? h->nnz : cap;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int s = ns[e], i = s / Z1, j = s - i * Z1;
+        atomicAdd(&cnt[(i / bh) * nb1 + j / bw], 1);
+    }
+}
+
+// exclusive prefix sum of cnt[0..n) into off[0..n] (off[n] = total) and a
+// copy into cur (the fill cursors); one CTA
+template <int NT>
+__global__ void __launch_bounds__(NT) bin_scan_kernel(const int *cnt, int *off, int *cur, int n, const WsHeader *h) {
+    if (h->overflow) return;
+    __shared__ int part[NT];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += NT) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? cnt[i] : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int d = 1; d < NT; d <<= 1) {  // inclusive scan (Hillis-Steele)
+            const int t = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        const int ex = carry + part[threadIdx.x] - v;
+        if (i < n) {
+            off[i] = ex;
+            cur[i] = ex;
+        }
+        __syncthreads();
+        if (threadIdx.x == NT - 1) carry += part[NT - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[n] = carry;
+}
+
+__global__ void bin_fill_kernel(const int *nk, const int *ns, const float *nzv, const WsHeader *h, long long cap,
+                                int *cur, int4 *list, int Z1, int bh, int bw, int nb1) {
+    if (h->overflow) return;
+    const long long n = h->nnz < cap ? h->nnz : cap;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int s = ns[e], i = s / Z1, j = s - i * Z1;
+        const int at = atomicAdd(&cur[(i / bh) * nb1 + j / bw], 1);
+        list[at] = make_int4(nk[e], i, j, __float_as_int(nzv[e]));
+    }
+}
+
+template <int NT, int KMAX>
+__global__ void __launch_bounds__(NT) gather_beta_kernel(GatherArgs a) {
+    if (a.h->overflow) return;
+    __shared__ int4 snz[kGatherStage];
+    const int r0 = blockIdx.y * a.bh, c0 = blockIdx.x * a.bw;
+    const int tr = threadIdx.x / a.bw;
+    const int i = r0 + tr, j = c0 + (threadIdx.x - tr * a.bw);
+    const bool live = tr < a.bh && i < a.Z0 && j < a.Z1;
+    const long long plane = (long long)a.Z0 * a.Z1;
+    const long long at = (long long)i * a.Z1 + j;
+    float acc[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; k++) acc[k] = (live && k < a.K) ? __ldcs(a.beta0 + k * plane + at) : 0.f;
+    // bins within L_i - 1 of the tile; the bins of one bin row are contiguous
+    // in the list.  Up to 32 bin rows at a time: their ranges are read in one
+    // go, then every staged nonzero in one pass.
+    __shared__ int s_beg[32], s_pre[33];
+    const int hr0 = max(0, r0 - (a.L0 - 1)), hr1 = min(a.Z0 - 1, r0 + a.bh - 1 + a.L0 - 1);
+    const int hc0 = max(0, c0 - (a.L1 - 1)), hc1 = min(a.Z1 - 1, c0 + a.bw - 1 + a.L1 - 1);
+    const int bc0 = hc0 / a.bw, bc1 = hc1 / a.bw;
+    for (int brg = hr0 / a.bh; brg <= hr1 / a.bh; brg += 32) {
+        const int nbr = min(32, hr1 / a.bh - brg + 1);
+        __syncthreads();
+        if (threadIdx.x < nbr) {
+            const int br = brg + threadIdx.x;
+            const int beg = __ldcg(a.off + br * a.nb1 + bc0), end = __ldcg(a.off + br * a.nb1 + bc1 + 1);
+            s_beg[threadIdx.x] = beg;
+            s_pre[threadIdx.x + 1] = end - beg;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_pre[0] = 0;
+            for (int r = 1; r <= nbr; r++) s_pre[r] += s_pre[r - 1];
+        }
+        __syncthreads();
+        const int total = s_pre[nbr];
+        for (int base = 0; base < total; base += kGatherStage) {
+            const int n = min(kGatherStage, total - base);
+            if (base > 0) __syncthreads();
+            for (int q = threadIdx.x; q < n; q += NT) {
+                int r = 0;
+                while (s_pre[r + 1] <= base + q) r++;
+                snz[q] = __ldcg(a.list + s_beg[r] + (base + q - s_pre[r]));
+            }
+            __syncthreads();
+            if (!live) continue;
+            for (int q = 0; q < n; q++) {
+                const int4 e = snz[q];
+                const int di = i - e.y, dj = j - e.z;
+                if (di <= -a.L0 || di >= a.L0 || dj <= -a.L1 || dj >= a.L1) continue;
+                const float z = __int_as_float(e.w);
+                // C_t[k'][delta][0..K): the K coefficients of the term, contiguous
+                const float4 *row = reinterpret_cast<const float4 *>(
+                    a.ct + ((size_t)(e.x * a.W0 + di + a.L0 - 1) * a.W1 + dj + a.L1 - 1) * a.Kp);
+                const int self = (di == 0 && dj == 0) ? e.x : -1;  // the term of (k, s) itself is left out
+#pragma unroll
+                for (int g = 0; g < KMAX / 4; g++) {
+                    if (4 * g >= a.K) break;
+                    const float4 c = __ldg(row + g);
+                    const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (4 * g + u != self) acc[4 * g + u] -= cv[u] * z;
+                }
+            }
+        }
+    }
+    unsigned long long m = 0;
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < KMAX; k++) {
+            if (k >= a.K) break;
+            a.beta[k * plane + at] = acc[k];
+            const double nk = a.nrm[k];
+            float dz = coord_update(acc[k], a.lambda, (float)nk, (float)(1.0 / nk)) - __ldcs(a.Z + k * plane + at);
+            dz = dz < 0.f ? -dz : dz;
+            const unsigned long long b = nonneg_bits(dz);
+            m = b > m ? b : m;
+        }
+    }
+    block_max_atomic<NT>(m, a.bits);
+}
+
 template <typename real>
 int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const real *X,
                    const real *D, const real *Z, real lambda, real *beta, cudaStream_t st,
@@ -232,22 +402,42 @@ int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const re
     if constexpr (sizeof(real) == 4) {
         if (from_beta0) {
             const float *b0 = reinterpret_cast<const float *>(ws + L.beta0);
-            copy_beta0_kernel<256><<<grid_for(nz / 4 + 1, 256), 256, 0, st>>>(b0, beta, nz, h);
-            LgcdArgs<float> a{};
-            a.beta = beta;
-            a.Z = const_cast<float *>(Z);
-            a.dtd = dtd;
-            a.K = g.K;
-            a.Z0 = g.Z0;
-            a.Z1 = g.Z1;
-            a.L0 = g.L0;
-            a.L1 = g.L1;
-            a.W0 = g.W0;
-            a.W1 = g.W1;
-            nz_window_kernel<256><<<152 * 8, 256, 0, st>>>(a, nk, ns, nzv, h, L.nnz_cap);
             const long long plane = g.nzpos();
-            dim3 grid((unsigned)std::min<long long>(ceil_div(plane, 4 * 256), std::max(1, 152 * 8 / g.K)), (unsigned)g.K);
-            maxdz_kernel<256><<<grid, 256, 0, st>>>(beta, Z, nrm, lambda, plane, h, &h->maxdz_bits);
+            if (g.K <= 32) {
+                const int nbins = L.gnb0 * L.gnb1;
+                int *cnt = reinterpret_cast<int *>(ws + L.gbin), *cur = cnt + nbins + 1;
+                int4 *list = reinterpret_cast<int4 *>(ws + L.glist);
+                float *ct = reinterpret_cast<float *>(ws + L.gtab);
+                const int W = g.W0 * g.W1;
+                ctab_kernel<<<grid_for((long long)g.K * W * L.gkp, 256), 256, 0, st>>>(dtd, ct, g.K, L.gkp, W);
+                CSC_CUDA(cudaMemsetAsync(cnt, 0, (size_t)nbins * sizeof(int), st));
+                bin_count_kernel<<<grid_for(L.nnz_cap, 256), 256, 0, st>>>(ns, h, L.nnz_cap, cnt, g.Z1, L.gbh,
+                                                                           L.gbw, L.gnb1);
+                bin_scan_kernel<1024><<<1, 1024, 0, st>>>(cnt, cnt, cur, nbins, h);
+                bin_fill_kernel<<<grid_for(L.nnz_cap, 256), 256, 0, st>>>(nk, ns, nzv, h, L.nnz_cap, cur, list, g.Z1,
+                                                                          L.gbh, L.gbw, L.gnb1);
+                GatherArgs ga{b0, Z, ct, beta, cnt, list, nrm, h, &h->maxdz_bits, lambda, g.K, L.gkp, g.Z0, g.Z1,
+                              g.L0, g.L1, g.W0, g.W1, L.gbh, L.gbw, L.gnb0, L.gnb1};
+                const int nt = L.gbh * L.gbw;  // 512 threads, one per position of the tile
+                gather_beta_kernel<512, 32><<<dim3((unsigned)L.gnb1, (unsigned)L.gnb0), nt, 0, st>>>(ga);
+            } else {
+                copy_beta0_kernel<256><<<grid_for(nz / 4 + 1, 256), 256, 0, st>>>(b0, beta, nz, h);
+                LgcdArgs<float> a{};
+                a.beta = beta;
+                a.Z = const_cast<float *>(Z);
+                a.dtd = dtd;
+                a.K = g.K;
+                a.Z0 = g.Z0;
+                a.Z1 = g.Z1;
+                a.L0 = g.L0;
+                a.L1 = g.L1;
+                a.W0 = g.W0;
+                a.W1 = g.W1;
+                nz_window_kernel<256><<<152 * 8, 256, 0, st>>>(a, nk, ns, nzv, h, L.nnz_cap);
+                dim3 grid((unsigned)std::min<long long>(ceil_div(plane, 4 * 256), std::max(1, 152 * 8 / g.K)),
+                          (unsigned)g.K);
+                maxdz_kernel<256><<<grid, 256, 0, st>>>(beta, Z, nrm, lambda, plane, h, &h->maxdz_bits);
+            }
             CSC_CUDA(cudaGetLastError());
             // overflow: the correlation of the (dense) residual instead
             return launch_corr_refresh<real>(g, Rr, D, Z, nrm, lambda, beta, &h->maxdz_bits, st, &h->overflow);
@@ -265,6 +455,11 @@ int preload_residual_kernels() {
         (const void *)recon_dense_kernel<float>,
         (const void *)residual_finish_kernel<float, 256>,
         (const void *)copy_beta0_kernel<256>,
+        (const void *)ctab_kernel,
+        (const void *)bin_count_kernel,
+        (const void *)bin_scan_kernel<1024>,
+        (const void *)bin_fill_kernel,
+        (const void *)gather_beta_kernel<512, 32>,
         (const void *)nz_window_kernel<256>,
         (const void *)maxdz_kernel<256>,
     };
