@@ -68,7 +68,11 @@ def parse():
                          "selection: LGCD / greedy / randomized / cyclic CD on one worker (Section 5.1); "
                          "lambda: 2-D solves over lambda x workers x {greedy, LGCD}")
     ap.add_argument("--cap", type=float, default=60.0, help="selection / lambda: seconds per solve")
-    ap.add_argument("--side", type=int, default=1024, help="image: side of the square image")
+    ap.add_argument("--side", type=int, default=1024,
+                    help="image: side of the square image; image4096: another side for the same family "
+                         "(profiling cases; default 4096)")
+    ap.add_argument("--sub", type=int, default=0,
+                    help="image4096 / cdl: sub-domain side (0: chosen by the autotuner, or 2 L with --no-tune)")
     ap.add_argument("--crop", type=int, default=512,
                     help="image4096: side of the crop of the same family that the oracle arms solve")
     ap.add_argument("--requests", type=int, default=512, help="served: requests in the trace")
@@ -724,9 +728,13 @@ def lambda_main(args):
 
 
 # ------------------------------------------------- the 4096^2 image (default)
-def large_image_workload():
-    from synthetic import IMAGE_4096
-    return IMAGE_4096
+def large_image_workload(side=4096):
+    """The 4096^2 workload, or an image of the same family at another side
+    (smaller cases for profiling)."""
+    from synthetic import IMAGE_4096, scaled
+    if side == 4096:
+        return IMAGE_4096
+    return scaled(IMAGE_4096, (side, side), f"csc2d_{side}x{side}_P1_K25_L32")
 
 
 def large_image_config(w, crop, extra=None):
@@ -779,7 +787,7 @@ def crop_oracle_solve(w, crop, seed):
 
 def large_image_main(args):
     rank, world, local = dist_env()
-    w = large_image_workload()
+    w = large_image_workload(args.side if args.side != 1024 or "--side" in sys.argv else 4096)
     crop = args.crop
     area = (crop * crop) / float(w.T[0] * w.T[1])
     if args.impl == "reference":
@@ -829,7 +837,9 @@ def large_image_main(args):
     s = pkg.make_shape(tuple(X.shape), tuple(Dd.shape))
     # sub-domain side by the autotuner, on another image of the family
     tune = None
-    if not args.no_tune:
+    if args.sub > 0:
+        tune = {"sub": args.sub, "ms": None, "tried": {}, "seconds": 0.0, "given": True}
+    elif not args.no_tune:
         from paper_1901_09235_gb300 import autotune
         t0 = time.perf_counter()
         tune = autotune.tune_single(make_image_device(w, args.seed + 1000 * rank + 2, D, device), Dd,
@@ -897,8 +907,12 @@ def large_image_main(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks["hbm_gbs"]) if "hbm_gbs" in peaks else 6800.0
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "6.8 TB/s (of fallback)"
-    traffic = profile_value("lgcd_global_kernel_csc2d_4096x4096_P1_K25_L32.md", "dram_bytes_per_launch",
-                            ("lgcd_global.cuh", "lgcd.cu", "lgcd_common.cuh", "common.cuh"))
+    # DRAM bytes per launch from the committed capture of this workload (sub-domains of 32), while the
+    # kernel sources match it
+    traffic = None
+    if w.T == (4096, 4096) and list(opts.sub) == [32, 32]:
+        traffic = profile_value("lgcd_global_kernel_csc2d_4096x4096_P1_K25_L32.md", "dram_bytes_per_launch",
+                                ("lgcd_global.cuh", "lgcd.cu", "lgcd_common.cuh", "common.cuh"))
     last = stats[-1]
     line = {
         "metric": METRIC, "value": world * args.steps / tot, "unit": UNIT, "n_gpus": world,
@@ -909,8 +923,9 @@ def large_image_main(args):
                                                "workers": last["workers"], "tiles": last["tiles"],
                                                "tile": last["tile_size"],
                                                "sub": list(opts.sub) if tune else [2 * l for l in w.L],
-                                               "sub_choice": "autotuned on another image of the family"
-                                               if tune else "library default (2 L)"}),
+                                               "sub_choice": ("given (--sub)" if tune and tune.get("given") else
+                                                              "autotuned on another image of the family"
+                                                              if tune else "library default (2 L)")}),
         "tuning": tune,
         "updates_per_s": world * upd / tot,
         "p50_ms": 1e3 * float(np.percentile(times, 50)),
@@ -1035,7 +1050,9 @@ def cdl_main(args):
     Dd = torch.empty_like(D0d)
     s = pkg.make_shape(tuple(X.shape), tuple(D0d.shape))
     tune = None
-    if not args.no_tune:
+    if args.sub > 0:
+        tune = {"sub": args.sub, "ms": None, "tried": {}, "seconds": 0.0, "given": True}
+    elif not args.no_tune:
         from paper_1901_09235_gb300 import autotune
         t0 = time.perf_counter()
         tune = autotune.tune_single(make_image_device(w, args.seed + 1000 * rank + 2, Dt, device), D0d,
