@@ -58,11 +58,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="image4096",
-                    choices=["image4096", "signal", "cdl", "served", "image", "selection", "lambda"],
+                    choices=["image4096", "signal", "cdl", "betainit", "served", "image", "selection", "lambda"],
                     help="image4096: the plain 4096^2 CSC solve, 25 atoms of 32 x 32 (default); "
                          "signal: the 1-D multichannel solve + dictionary step; "
                          "cdl: 10 outer iterations of Alg. 2 on an 8192^2 image, split-bf16 beta-init "
-                         "against plain FP32; "
+                         "against plain FP32; betainit: beta-init alone (FP32 CUDA cores and split bf16 on the "
+                         "tensor cores) on the 4096^2 family (--side); "
                          "served: the request trace through the continuous-batching server; "
                          "image: single solves of one served-family image (--side); "
                          "selection: LGCD / greedy / randomized / cyclic CD on one worker (Section 5.1); "
@@ -1167,6 +1168,72 @@ def cdl_main(args):
     return 0
 
 
+# ------------------------------------------------------- beta-init on its own
+def betainit_main(args):
+    """csc_init_beta (FP32, CUDA cores) and csc_init_beta_bf16x3 (split bf16 on
+    the tensor cores) on an image of the 4096^2 family, each timed with CUDA
+    events; the tensor-core arm against the bf16 peak (three products per
+    multiply-add of the correlation)."""
+    import torch
+    rank, world, local = dist_env()
+    side = args.side if "--side" in sys.argv else 4096
+    w = large_image_workload(side)
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "beta-init alone: the oracle arm is timed by "
+                              "the default workload (its solves include the oracle's beta-init)"}))
+        return 0
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1901_09235_gb300 as pkg
+    from synthetic import make_dictionary, make_image_device
+    D = make_dictionary(np.random.default_rng(args.seed), w.K, w.P, w.L)
+    Dd = torch.from_numpy(D).to(device)
+    X = make_image_device(w, args.seed + 1, D, device)
+    s = pkg.make_shape(tuple(X.shape), tuple(Dd.shape))
+    ws = pkg.workspace(s, device=device)
+    beta = torch.empty(pkg.z_shape(s), dtype=torch.float32, device=device)
+    dtd = torch.empty(pkg.tab_shape(s), dtype=torch.float32, device=device)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+    nz = int(np.prod(pkg.z_shape(s)))
+    flop = 2.0 * nz * w.P * int(np.prod(w.L))
+    out = {}
+    for name, fn in (("fp32", pkg.csc_init_beta), ("bf16x3", pkg.csc_init_beta_bf16x3)):
+        class Step:
+            def run(self):
+                fn(X, Dd, beta, dtd, ws, want_lambda_max=False)
+                return {}
+
+        times, _ = time_gpu(Step(), args.steps, max(3, args.warmup), flush, stream)
+        ms = 1e3 * sum(times) / len(times)
+        out[name] = {"ms": ms, "p50_ms": 1e3 * float(np.percentile(times, 50)), "tflops": flop / (ms / 1e3) / 1e12}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    Np = -(-w.K // 16) * 16
+    L1p = -(-w.L[1] // 16) * 16
+    # tensor work as issued: M = 128 positions x N = 2 Np (hi parts against the
+    # hi and lo dictionary) + N = Np (lo parts against the hi dictionary) per
+    # reduction step over P L0 L1p taps
+    tc_flop = 2.0 * nz * w.P * w.L[0] * L1p * 3 * Np / w.K
+    line = {"metric": "beta-init time (FP32 CUDA cores vs split bf16 on the tensor cores)",
+            "value": out["bf16x3"]["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "higher_is_better": False, "dtype": "bf16x3 (fp32 arm beside)",
+            "data": "synthetic", "config": {"workload": w.name, "K": w.K, "L": list(w.L), "P": w.P,
+                                            "flop": flop, "l2": "flushed between steps"},
+            "fp32": out["fp32"], "bf16x3": out["bf16x3"],
+            "roofline": {"bound": "tensor", "kernel": "corr_umma_kernel",
+                         "achieved": tc_flop / (out["bf16x3"]["ms"] / 1e3) / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                         "frac": tc_flop / (out["bf16x3"]["ms"] / 1e3) / 1e12 / bf16,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
+                         "note": "tensor work as issued (atoms padded to 16, taps to 16 per row, three products)"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.steps is None:
@@ -1180,6 +1247,8 @@ def main():
         return large_image_main(args)
     if args.workload == "cdl":
         return cdl_main(args)
+    if args.workload == "betainit":
+        return betainit_main(args)
     if args.workload == "served":
         return served_main(args)
     if args.workload == "selection":
