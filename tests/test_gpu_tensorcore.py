@@ -21,6 +21,11 @@ CASES = [
     Workload("tc25", P=1, K=25, T=(150, 290), L=(32, 32), density=1e-3, sigma=0.05, nonneg=True),
     Workload("tcserved", P=3, K=16, T=(97, 131), L=(12, 12), density=0.002, sigma=0.1),
     Workload("tc1tap", P=1, K=3, T=(200,), L=(1,), density=0.05, sigma=0.1),
+    # rows of X on 16-byte boundaries (T1 a multiple of 4): the builders' 16-byte
+    # loads, ragged last tiles included
+    Workload("tc1d_x4", P=5, K=10, T=(3004,), L=(64,), density=0.005, sigma=0.1),
+    Workload("tc25_x4", P=1, K=25, T=(150, 292), L=(32, 32), density=1e-3, sigma=0.05, nonneg=True),
+    Workload("tcserved_x4", P=3, K=16, T=(97, 132), L=(12, 12), density=0.002, sigma=0.1),
 ]
 
 
