@@ -892,10 +892,24 @@ def large_image_main(args):
         return st
 
     e2e_times, _ = time_gpu(step, args.steps, max(3, args.warmup), flush, stream, e2e=e2e_step)
+    # the mixed-precision form of the same solve: beta-init on the tensor cores
+    # in split bf16 (FP32 accumulation), beta / Z updates and the final KKT test
+    # in FP32, the same lambda (from the FP32 lambda_max, taken once)
+    lam_fixed = stats[-1]["lambda"]
+
+    class MixedStep:
+        def run(self):
+            pkg.csc_init_beta_bf16x3(X, Dd, beta, dtd, ws, want_lambda_max=False)
+            _, st = pkg.csc_lgcd_solve(X, Dd, dtd, beta, lam_fixed, w.tol, Z=Z, opts=opts, ws=ws)
+            if st["status"] != pkg.CSC_OK:
+                raise RuntimeError(f"solve status {st['status']}: {pkg.status_string(st['status'])}")
+            return st
+
+    mixed_times, mixed_stats = time_gpu(MixedStep(), args.steps, max(3, args.warmup), flush, stream)
     clk.__exit__(None, None, None)
     clocks = clk.summary()
     barrier()
-    tot, tot_e2e = max_over_ranks([sum(times), sum(e2e_times)], device)
+    tot, tot_e2e, tot_mixed = max_over_ranks([sum(times), sum(e2e_times), sum(mixed_times)], device)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -947,6 +961,14 @@ def large_image_main(args):
                 "d2h_bytes_per_step": int(Zh.numel() * 4 + 8)},
         "gpu_launches": sum(launches_per_step_solve(st) for st in stats),
         "clocks": clocks,
+        "mixed_bf16x3": {
+            "value": world * args.steps / tot_mixed, "unit": UNIT, "ms_per_step": 1e3 * tot_mixed / args.steps,
+            "step": "csc_init_beta_bf16x3 (tensor cores, split bf16, FP32 accumulation) + csc_lgcd_solve, "
+                    "the same lambda",
+            "objective": mixed_stats[-1]["objective"], "max_dz_final": mixed_stats[-1]["max_dz_final"],
+            "objective_rel_diff_vs_fp32": abs(mixed_stats[-1]["objective"] - last["objective"]) /
+                                          abs(last["objective"]),
+            "speedup_vs_fp32": tot / tot_mixed},
     }
     if not args.no_cpu_baseline and world == 1:
         # the oracle on crops of the same family, and the GPU on the same crop
