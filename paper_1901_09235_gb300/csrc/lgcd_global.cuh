@@ -262,16 +262,23 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         snrm[k] = real(a.nrm[k]);
         sinv[k] = real(1.0 / a.nrm[k]);
     }
-    int *flag = a.ctl + (size_t)w * kDirs * 32;  // this tile's counter
+    // this tile's notification counters, one per neighbour direction (each on
+    // its own 128-byte line): a neighbour in direction d bumps counter d
+    int *flag = a.ctl + (size_t)w * kDirs * 32;
     __shared__ Cand<real> s_red[2][NW];          // per-warp argmax, by iteration parity
-    __shared__ int s_ctl[2][2];                  // flag bumps seen, stop state
+    __shared__ int s_ctl[2][2];                  // bumps seen, stop state
     __shared__ real s_lo[NW], s_hi[NW];          // soft-lock maxima per warp
     __shared__ int s_pause;
     __shared__ volatile int s_block;  // a warp found a soft-lock blocker
     // state only thread 0 uses, kept out of every thread's registers
     __shared__ unsigned long long s_deadline;
     __shared__ real s_guard;
-    __shared__ int s_seen, s_cnt[5];  // updates, iterations, rejected, below tol, messages
+    __shared__ int s_seen[kDirs], s_cnt[5];  // bumps seen per direction; updates, iterations,
+                                             // rejected, below tol, messages
+    // sub-domains that the windows of the neighbour in direction d can reach
+    // (rows / columns within L_i - 1 of the shared edge or corner)
+    __shared__ unsigned long long s_dirmask[kDirs], s_wake;
+    __shared__ unsigned long long s_gm[2];  // sub-domains next to the directions of new bumps
     // nonzeros of Z per sub-domain (tiles of at most 64): counted from a cold
     // start, never below the true count; a sub-domain at zero is scanned
     // without reading Z
@@ -289,7 +296,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
             guard = real(g);
         }
         s_guard = guard;
-        s_seen = 0;
+        for (int d = 0; d < kDirs; d++) s_seen[d] = 0;
         for (int i = 0; i < 5; i++) s_cnt[i] = 0;
         for (int i = 0; i < 6; i++) s_ph[i] = 0;
         s_cand = 0;
@@ -303,26 +310,34 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
     // pause after M quiet iterations.
     const bool use_mask = M <= 64;
     for (int q = threadIdx.x; q < 64; q += NT) s_nz[q] = a.z_zero ? 0 : (1 << 24);
-    unsigned long long dmask = 0, ring = 0;
+    unsigned long long dmask = 0;
+    if (threadIdx.x < kDirs) s_dirmask[threadIdx.x] = 0;  // tiles of more than 64 sub-domains: unused
     if (use_mask) {
         dmask = M == 64 ? ~0ull : ((1ull << M) - 1ull);
-        for (int q = 0; q < M; q++) {
-            const int qr = q / ns1, qc = q - qr * ns1;
-            const int rr0 = qr * a.sub0, rr1 = min(h, rr0 + a.sub0), cc0 = qc * a.sub1, cc1 = min(wd, cc0 + a.sub1);
-            if (rr0 < a.L0 - 1 || rr1 > h - (a.L0 - 1) || cc0 < a.L1 - 1 || cc1 > wd - (a.L1 - 1))
-                ring |= 1ull << q;
+        if (threadIdx.x < kDirs) {
+            int dr, dc;
+            dir_offset(threadIdx.x, dr, dc);
+            // rows [ra, rb) x columns [ca, cb) of the tile that the windows of
+            // that neighbour reach
+            const int ra = dr > 0 ? h - (a.L0 - 1) : 0, rb = dr < 0 ? a.L0 - 1 : h;
+            const int ca = dc > 0 ? wd - (a.L1 - 1) : 0, cb = dc < 0 ? a.L1 - 1 : wd;
+            unsigned long long mk = 0;
+            for (int q = 0; q < M; q++) {
+                const int qr = q / ns1, qc = q - qr * ns1;
+                const int rr0 = qr * a.sub0, rr1 = min(h, rr0 + a.sub0), cc0 = qc * a.sub1, cc1 = min(wd, cc0 + a.sub1);
+                if (rr0 < rb && rr1 > ra && cc0 < cb && cc1 > ca) mk |= 1ull << q;
+            }
+            s_dirmask[threadIdx.x] = mk;
         }
     }
     int m = 0, quiet = 0, par = 0;
     __syncthreads();
     for (;;) {
-        // thread 0 reads this tile's flag counter and the stop word; the loads
-        // overlap its share of the scan
+        // lane d of warp 0 reads this tile's counter of direction d, thread 0
+        // the stop word; the loads overlap their share of the scan
         int f_now = 0, stop_now = 0;
-        if (threadIdx.x == 0) {
-            f_now = ld_relaxed(flag);
-            stop_now = ld_relaxed(&a.hdr->stop);
-        }
+        if (threadIdx.x < kDirs) f_now = ld_relaxed(flag + threadIdx.x * 32);
+        if (threadIdx.x == 0) stop_now = ld_relaxed(&a.hdr->stop);
         // ---- scan sub-domain m (Eq. gcd_candidate)
         const int mr = m / ns1, mc = m - mr * ns1;
         const int r0 = mr * a.sub0, c0 = mc * a.sub1;
@@ -364,23 +379,37 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
             }
         }
         c = warp_argmax(c);
-        if (threadIdx.x == 0) {
-            const unsigned long long t = clock64();
-            s_ph[0] += t - s_t;
-            s_t = t;
-            int got = 0, state = 0;
-            if (f_now != s_seen) {
-                got = f_now - s_seen;
-                s_seen = f_now;
-                atomicSub(&a.hdr->pending, got);  // observed: no longer in flight
+        if (warp == 0) {
+            // bumps per direction since the last look: their count and the
+            // directions they came from
+            int got = 0;
+            if (lane < kDirs) {
+                got = f_now - s_seen[lane];
+                s_seen[lane] = f_now;
             }
-            if (stop_now) state = 1;
-            else if (globaltimer_ns() > s_deadline) {
-                set_stop(a.hdr, CSC_ERR_TIMEOUT);
-                state = 1;
+            const int gmask = (int)(__ballot_sync(0xffffffffu, got != 0) & ((1u << kDirs) - 1u));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) got += __shfl_xor_sync(0xffffffffu, got, o);
+            if (lane == 0) {
+                const unsigned long long t = clock64();
+                s_ph[0] += t - s_t;
+                s_t = t;
+                int state = 0;
+                unsigned long long gm = 0;
+                if (got) {
+                    atomicSub(&a.hdr->pending, got);  // observed: no longer in flight
+                    for (int d = 0; d < kDirs; d++)
+                        if (gmask >> d & 1) gm |= s_dirmask[d];
+                }
+                s_gm[par] = gm;
+                if (stop_now) state = 1;
+                else if (globaltimer_ns() > s_deadline) {
+                    set_stop(a.hdr, CSC_ERR_TIMEOUT);
+                    state = 1;
+                }
+                s_ctl[par][0] = got;
+                s_ctl[par][1] = state;
             }
-            s_ctl[par][0] = got;
-            s_ctl[par][1] = state;
         }
         if (lane == 0) s_red[par][warp] = c;
         if (threadIdx.x == 0) s_block = 0;  // read after the barrier below
@@ -573,7 +602,10 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                         for (int i = 0; i < nd; i++) {
                             int dr, dc;
                             dir_offset(dl[i], dr, dc);
-                            atomicAdd(a.ctl + (size_t)((ta + dr) * a.G1 + (tb + dc)) * kDirs * 32, 1);
+                            // the receiver sees this tile in the opposite direction
+                            atomicAdd(a.ctl + (size_t)((ta + dr) * a.G1 + (tb + dc)) * kDirs * 32 +
+                                          (size_t)(kDirs - 1 - dl[i]) * 32,
+                                      1);
                         }
                         s_cnt[4] += nd;
                     }
@@ -601,7 +633,9 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                 for (int qr = qr0; qr <= qr1; qr++)
                     for (int qc = qc0; qc <= qc1; qc++) dmask |= 1ull << (qr * ns1 + qc);
             }
-            if (got > 0) dmask |= ring;
+            // sub-domains next to the neighbours that notified (this
+            // iteration's parity, flipped since)
+            dmask |= s_gm[par ^ 1];
             pause = dmask == 0;
         } else {
             quiet = (active || got > 0) ? 0 : quiet + 1;
@@ -613,7 +647,9 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                 atomicSub(&a.hdr->pending, 1);
                 int state = 0;
                 for (;;) {
-                    if (ld_relaxed(flag) != s_seen) {
+                    bool woken = false;
+                    for (int d = 0; d < kDirs; d++) woken |= ld_relaxed(flag + d * 32) != s_seen[d];
+                    if (woken) {
                         atomicAdd(&a.hdr->pending, 1);
                         break;
                     }
@@ -628,6 +664,13 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                     }
                     __nanosleep(256);
                 }
+                if (!state) {
+                    // the directions that woke this tile (at least one)
+                    unsigned long long wk = 0;
+                    for (int d = 0; d < kDirs; d++)
+                        if (ld_relaxed(flag + d * 32) != s_seen[d]) wk |= s_dirmask[d];
+                    s_wake = wk;
+                }
                 s_pause = state;
                 const unsigned long long t = clock64();
                 s_ph[5] += t - s_t;
@@ -636,8 +679,9 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
             __syncthreads();
             if (s_pause) break;
             quiet = 0;
-            // woken by a flag bump: beta along the border band has changed
-            dmask |= ring;
+            // woken by a notification: beta next to that neighbour has changed
+            // (the next iteration reads the counters and accounts for the bumps)
+            if (use_mask) dmask |= s_wake;
             if (use_mask && dmask == 0) dmask = M == 64 ? ~0ull : ((1ull << M) - 1ull);
         }
         if (use_mask) {

@@ -270,3 +270,23 @@ def test_global_tiles_refuse_beta_or_z_off_a_16_byte_boundary(pkg, orc):
     with pytest.raises(pkg.CscError) as e:
         pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, 0.1 * lm, 1e-4, Z=Zoff, opts=pkg.default_opts(placement=2))
     assert e.value.status == pkg.CSC_ERR_INVALID
+
+
+def test_global_tiles_with_more_than_64_subdomains_per_tile(pkg, orc):
+    """Tiles of more than 64 sub-domains keep no dirty mask: they scan
+    cyclically, pause after a quiet sweep and wake on any neighbour's
+    notification.  Same bar as the other global-tile cases."""
+    w = ASYNC[3]
+    X, D, _ = make_problem(w, 37)
+    lam = 0.1 * orc.lambda_max(X, D)
+    tol = 1e-4
+    ref = orc.lgcd(X, D, lam, tol)
+    Xd, Dd = dev(X), dev(D)
+    beta, dtd, _ = pkg.csc_init_beta(Xd, Dd)
+    opts = pkg.default_opts(placement=2, sub=(2, 2), tile=(40, 46))
+    Z, st = pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, lam, tol, opts=opts)
+    assert st["status"] == 0 and st["placement"] == 2 and st["workers"] > 4, st
+    Zh = host(Z)
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    assert abs(orc.objective(X, D, Zh, lam) - f_ref) <= 1e-5 * abs(f_ref)
+    assert kkt_fp64_within_bound(orc, X, D, Zh, lam, tol)[0]
