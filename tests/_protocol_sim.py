@@ -7,11 +7,11 @@ interleavings, delayed notifications, lock-step rounds.
 Everything is FP64, on a 1-D (T0 = L0 = 1) or 2-D problem: X (P, T0, T1),
 D (K, P, L0, L1).  Shared state is what the GPU keeps in global memory: beta
 and Z over the whole activation domain, one notification counter per tile
-and the `pending` count of active workers plus notifications not yet
-observed.  A worker is a generator that yields at every point where another
-worker may run: after reading its flag, after the scan, after the soft-lock
+and neighbour direction, and the `pending` count of active workers plus
+notifications not yet observed.  A worker is a generator that yields at every point where another
+worker may run: after reading its counters, after the scan, after the soft-lock
 test, after writing Z and after each chunk of rows of its window update (so
-neighbours see a half-applied window).  Notifications (flag increments)
+neighbours see a half-applied window).  Notifications (counter increments)
 reach their tile after a delay the scheduler draws.
 
 The worker's steps mirror the kernel (paper_1901_09235_gb300/csrc/
@@ -21,9 +21,12 @@ below eps; a candidate whose window V(s0) leaves the tile is accepted only if
 its |dZ| is above every |dZ| in V(s0) held by a lower-index tile and not below
 any held by a higher-index one (Eq. soft_lock, ties to the lower row-major
 tile index); an accepted update writes Z, subtracts C[k][k0][s - s0] dZ from
-beta over V(s0) (Eq. beta_update) and notifies the tiles V(s0) reaches; a
-worker whose sub-domains are all clean pauses (pending - 1) until a
-notification arrives (pending + 1) or pending reaches 0.
+beta over V(s0) (Eq. beta_update) and notifies the tiles V(s0) reaches,
+each on its counter for the direction the sender lies in; a bump marks dirty
+the sub-domains of the receiver within L - 1 of the edge or corner it shares
+with the sender; a worker whose sub-domains are all clean pauses
+(pending - 1) until a notification arrives (pending + 1) or pending
+reaches 0.
 
 This module is test infrastructure: it shares nothing with the CUDA library."""
 from __future__ import annotations
@@ -108,7 +111,9 @@ class Sim:
         self.guard = guard
         self.beta = pb.beta_init()
         self.Z = np.zeros_like(self.beta)
-        self.flag = [0] * self.G
+        # flag[w][(dr, dc)]: bumps tile w received from its neighbour at
+        # tile-grid offset (dr, dc)
+        self.flag = [dict() for _ in range(self.G)]
         self.pending = self.G
         self.in_flight = []  # [deliver at tick, tile]
         self.tick = 0
@@ -138,22 +143,31 @@ class Sim:
         def in_band(i, j):
             return (i - r0 < L0 - 1 or i - r0 >= h - (L0 - 1) or j - c0 < L1 - 1 or j - c0 >= wd - (L1 - 1))
 
-        ring = set()
-        for q in range(M):
-            a0, a1, b0, b1 = box(q)
-            if a0 - r0 < L0 - 1 or a1 - r0 > h - (L0 - 1) or b0 - c0 < L1 - 1 or b1 - c0 > wd - (L1 - 1):
-                ring.add(q)
+        def facing(d):
+            """Sub-domains within L - 1 of the edge or corner shared with the
+            neighbour at offset d."""
+            dr, dc = d
+            ra, rb = (h - (L0 - 1) if dr > 0 else 0), (L0 - 1 if dr < 0 else h)
+            ca, cb = (wd - (L1 - 1) if dc > 0 else 0), (L1 - 1 if dc < 0 else wd)
+            out = set()
+            for q in range(M):
+                a0, a1, b0, b1 = box(q)
+                if a0 - r0 < rb and a1 - r0 > ra and b0 - c0 < cb and b1 - c0 > ca:
+                    out.add(q)
+            return out
+
         dirty = set(range(M))
-        seen, m = 0, 0
+        seen, m = {}, 0
         while True:
-            f_now = self.flag[w]
+            f_now = dict(self.flag[w])
             yield
             if self.stop:
                 return
-            got = f_now - seen
+            new = {d: n - seen.get(d, 0) for d, n in f_now.items() if n != seen.get(d, 0)}
+            got = sum(new.values())
             if got:
                 self.pending -= got
-                seen = f_now
+                seen.update({d: f_now[d] for d in new})
             # scan C_m
             a0, a1, b0, b1 = box(m)
             best = None
@@ -215,7 +229,9 @@ class Sim:
                         self.pending += len(targets)
                         for tw in sorted(targets):
                             delay = 1 if self.schedule == "lockstep" else int(self.rng.integers(0, self.max_delay + 1))
-                            self.in_flight.append([self.tick + delay, tw])
+                            # the receiver sees this tile at the opposite offset
+                            d = (ta - tw // self.G1, tb - tw % self.G1)
+                            self.in_flight.append([self.tick + delay, tw, d])
                     for q in range(M):
                         q0, q1, p0, p1 = box(q)
                         if q0 < v[1] and q1 > v[0] and p0 < v[3] and p1 > v[2]:
@@ -224,14 +240,19 @@ class Sim:
                     self.rejected += 1
             else:
                 dirty.discard(m)
-            if got:
-                dirty |= ring
+            for d in new:
+                dirty |= facing(d)
             if not dirty:
                 self.pending -= 1
                 while True:
-                    if self.flag[w] != seen:
+                    woke = [d for d, n in self.flag[w].items() if n != seen.get(d, 0)]
+                    if woke:
+                        # the bumps themselves are accounted for by the next
+                        # iteration's read of the counters
                         self.pending += 1
-                        dirty |= ring or set(range(M))
+                        for d in woke:
+                            dirty |= facing(d)
+                        dirty = dirty or set(range(M))
                         break
                     if self.pending == 0 or self.stop:
                         return
@@ -241,11 +262,11 @@ class Sim:
 
     def deliver(self):
         keep = []
-        for at, tw in self.in_flight:
+        for at, tw, d in self.in_flight:
             if at <= self.tick:
-                self.flag[tw] += 1
+                self.flag[tw][d] = self.flag[tw].get(d, 0) + 1
             else:
-                keep.append([at, tw])
+                keep.append([at, tw, d])
         self.in_flight = keep
 
     def run(self, max_ticks=2_000_000):
