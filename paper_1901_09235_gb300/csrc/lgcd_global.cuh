@@ -16,20 +16,23 @@ namespace csc {
 // red.global.add, so updates from neighbouring tiles that land in the same
 // entries add up instead of overwriting each other, and an update whose
 // window V(s0) crosses into a neighbour is applied there directly.  The
-// neighbour learns that its beta changed through its flag counter (one word
-// per tile): a worker bumps the counter of every tile V(s0) reaches.  The
-// counters carry the same termination accounting as the mailboxes of the
+// neighbour learns that its beta changed through its notification counters
+// (one per neighbour direction): a worker bumps, in every tile V(s0) reaches,
+// the counter of the direction it lies in.  The counters carry the same termination accounting as the mailboxes of the
 // shared-memory variant: `pending` counts active workers plus flag bumps not
 // yet observed by their tile.  One sub-domain per iteration, scanned and
 // updated by the whole CTA.
 // Threads per worker CTA of the single-solve kernel (two CTAs per SM).
-// Measured on the 4096^2 image (25 atoms of 32 x 32): 304 x 512, 456 x 256,
-// 608 x 256 and 304 x 384 threads all solve in the same time (45 ms), the
-// shorter per-tile chains of more tiles offset by slower iterations.
-constexpr int kGlobThreads = 512;
+// Measured on the 4096^2 image (25 atoms of 32 x 32): 456 x 256, 608 x 256
+// and 304 x 512 threads solve in the same time, the shorter per-tile chains
+// of more tiles offset by slower iterations; with 304 tiles, 448 threads (72
+// registers each) take 41.1 ms, 384 (80) 42.1 ms, 512 (64, a few spills in
+// the soft-lock path) 42.9 ms and 320 44.3 ms.
+constexpr int kGlobThreads = 448;
 // Tasks whose loads a thread issues together in the FP32 scan and window
-// update: two each fit the 64 registers of two 512-thread CTAs per SM without
-// spilling; three to six (with spills) were slower on the 4096^2 image.
+// update: two each fit the registers of two CTAs per SM without spilling;
+// three (384 threads) and three to six (512, with spills) were slower on the
+// 4096^2 image.
 constexpr int kScanBatch = 2, kWindowBatch = 2;
 // Boxes of K x rows x cols are walked in units of (atom, block of RB rows,
 // 32-column chunk): a warp takes units NW apart, issues the loads of all rows
@@ -122,7 +125,12 @@ __device__ __forceinline__ Cand<float> scan_v4(const LgcdArgs<float> &a, const f
     const unsigned plane_lo = (unsigned)plane, base_lo = (unsigned)(or0 + r0) * (unsigned)a.Z1 + oc0 + c0;
     const int NG = (bw + 6) >> 2;  // groups of 4 that can meet bw columns
     const int total = K * bh * NG;
-    Cand<float> c{-1.f, 0xffffffffu, 0.f, 0.f};
+    // the thread's best |dZ| so far, with Z', dZ and its position (task
+    // index x 4 + element): a thread keeps the first of equal |dZ| in its
+    // own (atom-major) order, and the key ((row-major tile position) x K + k)
+    // that the warp and block reductions compare is built once, at the end
+    float ba = -1.f, bzn = 0.f, bdz = 0.f;
+    int bt = -1;
     TaskStep ts;
     ts.init(threadIdx.x, NT, bh, NG);
     for (int t = threadIdx.x; t < total; t += B * NT) {
@@ -160,7 +168,7 @@ __device__ __forceinline__ Cand<float> scan_v4(const LgcdArgs<float> &a, const f
         rs.j = j_s;
 #pragma unroll
         for (int u = 0; u < B; u++) {
-            const int k = rs.k, li = r0 + rs.r;
+            const int k = rs.k;
             const int sft = (int)((k * plane_lo + base_lo + (unsigned)rs.r * (unsigned)a.Z1) & 3u);
             const int lj0 = c0 + 4 * rs.j - sft;  // tile column of the group's first lane
             rs.next();
@@ -174,13 +182,25 @@ __device__ __forceinline__ Cand<float> scan_v4(const LgcdArgs<float> &a, const f
                 if (lj >= c0 && lj < c0 + bw) {
                     const float zn = coord_update(b4[e], a.lambda, nk, ik);
                     const float dz = zn - z4[e];
-                    Cand<float> x{dz < 0.f ? -dz : dz, (unsigned)((li * a.t1 + lj) * K + k), zn, dz};
-                    if (better(x, c)) c = x;
+                    const float ad = fabsf(dz);
+                    const int t4 = (t + u * NT) * 4 + e;
+                    if (ad > ba) {
+                        ba = ad;
+                        bt = t4;
+                        bzn = zn;
+                        bdz = dz;
+                    }
                 }
             }
         }
     }
-    return c;
+    unsigned key = 0xffffffffu;
+    if (bt >= 0) {
+        const int per_k = bh * NG, t = bt >> 2, k = t / per_k, rem = t - k * per_k, r = rem / NG, j = rem - r * NG;
+        const int sft = (int)((k * plane_lo + base_lo + (unsigned)r * (unsigned)a.Z1) & 3u);
+        key = (unsigned)(((r0 + r) * a.t1 + c0 + 4 * j - sft + (bt & 3)) * K + k);
+    }
+    return Cand<float>{ba, key, bzn, bdz};
 }
 
 // beta_k[s] -= C[k][k0][s - s0] dz over V(s0) within the domain, except
