@@ -148,8 +148,10 @@ def test_cdl_step_matches_the_separate_calls(pkg, orc, w):
 def test_chained_cdl_steps_with_a_fixed_lambda_follow_cdl_fit(pkg, orc):
     """Two cdl_step calls, the second with the first one's lambda, solve the
     fixed problem of Alg. 2 as cdl_fit's first two iterations do: the costs
-    after each CSC step agree (the solves are asynchronous, so within the
-    solve tolerance, not bit for bit) and so do the dictionaries.  ||X||^2 is
+    after each CSC step agree and so do the dictionaries.  The solves are
+    asynchronous: each stops somewhere in the set where max |dZ| < tol (Alg. 1
+    stops there, not at the optimum), and two runs of the same solve spread
+    by about 1.1e-5 relative on this image, so costs are compared at 5e-5.  ||X||^2 is
     summed on the device; beta-init in FP32 and, for the second call, on the
     tensor cores."""
     w = Workload("chain96", P=1, K=4, T=(96, 96), L=(8, 8), density=5e-3, sigma=0.05, nonneg=True)
@@ -170,7 +172,7 @@ def test_chained_cdl_steps_with_a_fixed_lambda_follow_cdl_fit(pkg, orc):
                              opts=pkg.default_opts(beta_init=beta_init))
         assert s1["status"] == 0 and s2["status"] == 0 and s2["lambda"] == lam
         for st, (c_csc, _) in zip((s1, s2), tr):
-            assert abs(st["objective"] - c_csc) <= 1e-5 * abs(c_csc), (st["objective"], c_csc)
+            assert abs(st["objective"] - c_csc) <= 5e-5 * abs(c_csc), (st["objective"], c_csc)
         assert np.allclose(host(D), host(Dfit), rtol=0, atol=1e-3)
         # the same cost on the oracle's side: its loop with the same fixed lambda
         _, _, tr_ref = orc.cdl(X, D0, 0.1, 1e-4, 2, pgd_max_iter=20)
