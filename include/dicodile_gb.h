@@ -78,7 +78,9 @@ typedef struct {
 } csc_shape;
 
 typedef struct {
-    int tile[2];          /* worker tile per dimension (0 = planned automatically)        */
+    int tile[2];          /* worker tile per dimension (0 = planned automatically; at least
+                             L_i, and at least 2 L_i - 1 for asynchronous tiles in global
+                             memory, else CSC_ERR_INVALID)                              */
     int sub[2];           /* LGCD sub-domain per dimension (0 = 2 L_i, Section 3)          */
     int mode;             /* enum csc_mode                                                 */
     int max_workers;      /* upper bound on the number of tiles (0 = all co-resident)      */

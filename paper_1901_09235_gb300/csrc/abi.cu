@@ -108,6 +108,12 @@ WsLayout plan_workspace(const Geom &g, int max_workers, int rs) {
         o2 = align256(o2 + (size_t)L.nnz_cap * 16);
         L.gtab = o2;
         o2 = align256(o2 + (size_t)g.K * g.W0 * g.W1 * L.gkp * sizeof(float));
+        // rows of W1 values with 4 zeros before and at least 4 after, the row
+        // stride equal to Z1 mod 4; blocks a multiple of 16 bytes
+        L.wrs = g.W1 + 8 + ((g.Z1 - (g.W1 + 8)) & 3);
+        L.wbs = (g.W0 * L.wrs + 3) / 4 * 4;
+        L.wtab = o2;
+        o2 = align256(o2 + (size_t)g.K * g.K * L.wbs * sizeof(float));
         L.total_beta0 = o2;
     } else {
         L.total_beta0 = off;

@@ -79,6 +79,10 @@ struct WsLayout {
     // offsets and cursors, its binned nonzero list and the transposed table
     size_t gbin, glist, gtab;
     int gbh, gbw, gnb0, gnb1, gkp;  // bin rows / columns, bins per dimension, padded K
+    // and the table in the window layout of the staged window update: K x K
+    // blocks [k0][k] of wbs floats, W0 rows of wrs floats each
+    size_t wtab;
+    int wrs, wbs;
     long long nnz_cap;
     int max_workers;
     int blk_cap;

@@ -168,7 +168,23 @@ __global__ void __launch_bounds__(NT, 1) lgcd_phased_kernel(LgcdArgs<real> a) {
 template <typename real>
 __global__ void __launch_bounds__(kGlobThreads, 2) lgcd_global_kernel(LgcdArgs<real> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    global_tile_worker<real, kGlobThreads, 6>(a, blockIdx.x, smem_raw);
+    global_tile_worker<real, kGlobThreads, 4, true>(a, blockIdx.x, smem_raw);
+}
+
+// The table in the window layout of the staged window update: block
+// [k0][k] = C[k][k0] as W0 rows of wrs floats, row rw's values at
+// rw * wrs + 4 + cw, zeros elsewhere, and the centre of C[k0][k0] zeroed.
+__global__ void wtab_kernel(const float *dtd, float *wtab, int K, int W0, int W1, int L0, int L1, int wrs, int wbs) {
+    const long long n = (long long)K * K * wbs;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / wbs), r = (int)(i - (long long)b * wbs);
+        const int k0 = b / K, k = b - k0 * K;
+        const int rw = r / wrs, cw = r - rw * wrs - 4;
+        float v = 0.f;
+        if (rw < W0 && cw >= 0 && cw < W1 && !(k == k0 && rw == L0 - 1 && cw == L1 - 1))
+            v = dtd[(((size_t)k * K + k0) * W0 + rw) * W1 + cw];
+        wtab[i] = v;
+    }
 }
 
 // Header reset before a launch: pending = number of workers, counters 0.
@@ -315,6 +331,10 @@ int make_plan_global(const Geom &g, const csc_solve_opts &o, long long max_w, in
         const int t0 = d1 ? 1 : (ut0 > 0 ? std::min(ut0, g.Z0) : g.Z0);
         const int t1 = ut1 > 0 ? std::min(ut1, g.Z1) : g.Z1;
         if ((t0 < g.L0 && t0 < g.Z0) || (t1 < g.L1 && t1 < g.Z1)) return CSC_ERR_INVALID;
+        // the soft-lock of a global-memory tile tests one strip per dimension:
+        // no window V(s0) may cross both edges of a tile
+        if (o.mode == CSC_MODE_ASYNC && ((t0 < 2 * g.L0 - 1 && t0 < g.Z0) || (t1 < 2 * g.L1 - 1 && t1 < g.Z1)))
+            return CSC_ERR_INVALID;
         pl->t0 = t0;
         pl->t1 = t1;
     } else {
@@ -404,6 +424,20 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     const int W = pl.G0 * pl.G1;
     WsLayout L = plan_workspace(g, W, rs);
     if (ws_bytes < L.total) return CSC_ERR_WORKSPACE;
+    // FP32 global tiles with the optional workspace region: the window update
+    // stages the table through as many shared-memory slots (up to 4) as fit
+    // beside a second CTA on the SM; fewer than 2 and it reads dtd instead
+    int wslots = 0;
+    if (global && rs == 4 && ws_bytes >= L.total_beta0) {
+        cudaFuncAttributes fa;
+        CSC_CUDA(cudaFuncGetAttributes(&fa, kern));
+        const long long slot = ((long long)L.wbs + 8) * 4;
+        const long long budget =
+            (long long)smem_per_sm() / 2 - 1024 - (long long)fa.sharedSizeBytes - (long long)stage_offset(g.K);
+        wslots = (int)std::min<long long>(kMaxStageSlots, std::max<long long>(0, budget / slot));
+        if (wslots < 2) wslots = 0;
+        if (wslots) pl.smem = stage_offset(g.K) + (size_t)wslots * (size_t)slot;
+    }
     unsigned char *wsb = static_cast<unsigned char *>(ws);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(wsb + L.hdr);
     double *nrm = reinterpret_cast<double *>(wsb + L.nrm);
@@ -440,8 +474,17 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     if (use_beta0) CSC_CUDA(cudaMemcpyAsync(wsb + L.beta0, beta, (size_t)g.nz() * rs, cudaMemcpyDeviceToDevice, st));
     rc = launch_atom_norms<real>(g, D, nrm, dmax, st);
     if (rc) return rc;
+    float *wtab = reinterpret_cast<float *>(wsb + L.wtab);
+    if constexpr (sizeof(real) == 4) {
+        if (wslots) {
+            const long long n = (long long)g.K * g.K * L.wbs;
+            wtab_kernel<<<(unsigned)std::min<long long>(4096, (n + 255) / 256), 256, 0, st>>>(
+                dtd, wtab, g.K, g.W0, g.W1, g.L0, g.L1, L.wrs, L.wbs);
+            CSC_CUDA(cudaGetLastError());
+        }
+    }
 
-    LgcdArgs<real> a;
+    LgcdArgs<real> a{};
     a.beta = beta;
     a.Z = Z;
     a.dtd = dtd;
@@ -473,6 +516,10 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
     const double margin = o.stop_margin > 0.0 ? o.stop_margin : (sizeof(real) == 4 ? 0.99 : 1.0);
     a.eps = real(margin) * tol;
     a.max_updates = o.max_updates;
+    a.wtab = wslots ? wtab : nullptr;
+    a.wrs = L.wrs;
+    a.wbs = L.wbs;
+    a.wslots = wslots;
     double tmo = o.timeout_s > 0 ? o.timeout_s : 30.0;
     a.timeout_ns = (unsigned long long)(tmo * 1e9);
     {

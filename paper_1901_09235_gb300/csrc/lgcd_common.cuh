@@ -28,6 +28,11 @@ struct LgcdArgs {
     real lambda, eps;
     long long max_updates;
     unsigned long long timeout_ns;
+    // FP32 global tiles of the single-solve kernel: the table in its window
+    // layout (null: the window update reads dtd), its row and block strides
+    // in floats and the number of shared-memory slots that stage it
+    const float *wtab;
+    int wrs, wbs, wslots;
 };
 
 template <typename real>

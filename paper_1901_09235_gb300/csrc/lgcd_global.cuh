@@ -12,7 +12,8 @@ namespace csc {
 // ============================================================ GLOBAL TILES
 // Variant for tiles whose beta / Z / table do not fit in shared memory (large
 // atoms, e.g. 25 atoms of 32 x 32).  beta and Z stay in global memory (HBM,
-// L2) and the table is read from L2.  Every beta window update is a
+// L2); the table is read from L2, or (single-solve FP32 kernel) staged
+// through shared memory by bulk copies, one block C[k][k0] at a time.  Every beta window update is a
 // red.global.add, so updates from neighbouring tiles that land in the same
 // entries add up instead of overwriting each other, and an update whose
 // window V(s0) crosses into a neighbour is applied there directly.  The
@@ -37,10 +38,11 @@ constexpr int kScanBatch = 2, kWindowBatch = 2;
 // Boxes of K x rows x cols are walked in units of (atom, block of RB rows,
 // 32-column chunk): a warp takes units NW apart, issues the loads of all rows
 // of its unit, then evaluates them.  Two divisions per unit, none per
-// element.  RB is the largest block a kernel holds in registers without
-// spilling.
+// element.  RB is at most the largest block a kernel holds in registers
+// without spilling (the single-solve kernel takes 4: 6 and 8 spill nothing
+// but were 2 % slower on the 4096^2 image, 5 was 7 % slower).
 
-template <typename real, int NT, int RB>
+template <typename real, int NT, int RB, bool STAGED = false>
 __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char *smem_raw);
 
 // Warp argmax with the oracle's tie-break (larger |dZ|, then smaller key);
@@ -258,17 +260,178 @@ __device__ __forceinline__ void window_v4(const LgcdArgs<float> &a, int k0, int 
     }
 }
 
+// ------------------------------------------------ staged window update
+// The single-solve FP32 kernel stages the K blocks C[k][k0] (k = 0..K-1) of
+// an update in shared memory: a ring of a.wslots slots, each filled by one
+// bulk copy (cp.async.bulk) whose completion lands on the slot's mbarrier,
+// so that the table reads of an update overlap one another and the
+// reductions instead of costing one L2 round trip per group of four.  The
+// workspace copy of the table is laid out for it: block (k0, k) holds W0 rows
+// of wrs floats, row rw's W1 values starting at rw * wrs + 4 with zeros
+// around them, and the centre of C[k0][k0] is 0 (an update leaves beta at
+// (k0, s0) itself alone).  Because wrs = Z1 (mod 4), the four values of every
+// 16-byte group of beta in one block start at the same offset mod 4 of the
+// slot: two aligned 16-byte loads and a fixed selection per block.
+constexpr int kMaxStageSlots = 4;
+
+// Byte offset of the first slot in the worker's dynamic shared memory (after
+// the 2 K atom norms and inverses, 128-byte aligned).
+__host__ __device__ constexpr size_t stage_offset(int K) { return ((size_t)2 * K * 8 + 127) & ~(size_t)127; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void stage_issue(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Waits for the phase of the given parity of a slot's mbarrier; false after
+// 100 ms (a bulk copy of a few kB lands in microseconds).
+__device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (globaltimer_ns() - t0 > 100000000ull) return false;
+    }
+}
+
+// beta_k[s] -= C[k][k0][s - s0] dz over the window rows of atom k, the
+// block C[k][k0] read from a slot; CP = the slot offset mod 4 of every group.
+template <int NT, int CP>
+__device__ __forceinline__ void window_block(const LgcdArgs<float> &a, const float *blk, int k, int gi0, int gjs,
+                                             bool col_edge, float dz) {
+    const long long plane = (long long)a.Z0 * a.Z1, nall = (long long)a.K * plane;
+    const int W1 = a.W1, RS = a.wrs, NG = (W1 + 6) >> 2;
+    for (int t = threadIdx.x; t < a.W0 * NG; t += NT) {
+        const int rw = t / NG, j = t - rw * NG;
+        const int gi = gi0 + rw - (a.L0 - 1);
+        if (gi < 0 || gi >= a.Z0) continue;
+        const long long row = (long long)k * plane + (long long)gi * a.Z1 + gjs;  // window column 0
+        const int cw0 = 4 * j - (int)(row & 3);  // window column of the group's first lane
+        if (cw0 >= W1) continue;
+        const int idx = rw * RS + 4 + cw0;
+        float c[4];
+        if ((idx & 3) == CP) {
+            const float *p = blk + (idx - CP);  // 16-byte aligned
+            const float4 lo = *reinterpret_cast<const float4 *>(p);
+            if constexpr (CP == 0) {
+                c[0] = lo.x;
+                c[1] = lo.y;
+                c[2] = lo.z;
+                c[3] = lo.w;
+            } else {
+                const float4 hi = *reinterpret_cast<const float4 *>(p + 4);
+                const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) c[e] = v[CP + e];
+            }
+        } else {  // not reached (wrs = Z1 mod 4); element by element
+#pragma unroll
+            for (int e = 0; e < 4; e++) c[e] = blk[idx + e];
+        }
+        if (col_edge) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int gj = gjs + cw0 + e;
+                if (gj < 0 || gj >= a.Z1) c[e] = 0.f;
+            }
+        }
+        const long long gf = row + cw0;
+        if (gf >= 0 && gf + 3 < nall) {
+            red_add_v4(a.beta + gf, -(c[0] * dz), -(c[1] * dz), -(c[2] * dz), -(c[3] * dz));
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (gf + e >= 0 && gf + e < nall && c[e] != 0.f) atomicAdd(a.beta + gf + e, -(c[e] * dz));
+        }
+    }
+}
+
+// The window update of an accepted candidate (k0, (gi0, gj0)) through the
+// staged table.  q counts the blocks this CTA has consumed (the same value
+// in every thread).  Returns false when a copy did not land in time; the
+// copies still in flight are then waited for once more and the caller stops
+// the solve.
+template <int NT>
+__device__ bool window_staged(const LgcdArgs<float> &a, float *ring, uint64_t *bars, unsigned &q, int k0, int gi0,
+                              int gj0, float dz) {
+    const int K = a.K, S = a.wslots, slotf = a.wbs + 8;
+    const long long plane = (long long)a.Z0 * a.Z1;
+    const int gjs = gj0 - (a.L1 - 1);
+    const bool col_edge = gjs < 0 || gj0 + a.L1 - 1 >= a.Z1;
+    const float *src0 = a.wtab + (size_t)k0 * K * a.wbs;
+    const uint32_t bytes = (uint32_t)a.wbs * 4u;
+    const int first = min(S, K);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < first; i++) {
+            const int sl = (int)((q + i) % (unsigned)S);
+            stage_issue(smem_u32(ring + (size_t)sl * slotf), src0 + (size_t)i * a.wbs, bytes, smem_u32(&bars[sl]));
+        }
+    int issued = first;
+    bool ok = true;
+    int k = 0;
+    for (; k < K; k++) {
+        const unsigned n = q + k;
+        const int sl = (int)(n % (unsigned)S);
+        const bool mine = stage_wait(smem_u32(&bars[sl]), (n / (unsigned)S) & 1u);
+        if (mine) {
+            const long long row0 = (long long)k * plane + (long long)(gi0 - (a.L0 - 1)) * a.Z1 + gjs;
+            const int cp = (4 - (int)(row0 & 3)) & 3;
+            const float *blk = ring + (size_t)sl * slotf;
+            switch (cp) {
+                case 0: window_block<NT, 0>(a, blk, k, gi0, gjs, col_edge, dz); break;
+                case 1: window_block<NT, 1>(a, blk, k, gi0, gjs, col_edge, dz); break;
+                case 2: window_block<NT, 2>(a, blk, k, gi0, gjs, col_edge, dz); break;
+                default: window_block<NT, 3>(a, blk, k, gi0, gjs, col_edge, dz); break;
+            }
+        }
+        // every thread is done with the slot (and agrees on the outcome)
+        ok = __syncthreads_and(mine) != 0;
+        if (!ok) break;
+        if (threadIdx.x == 0 && k + S < K) {
+            stage_issue(smem_u32(ring + (size_t)sl * slotf), src0 + (size_t)(k + S) * a.wbs, bytes,
+                        smem_u32(&bars[sl]));
+        }
+        if (k + S < K) issued++;
+    }
+    if (!ok && threadIdx.x == 0) {
+        // blocks k .. issued - 1 may still be in flight: one more bounded wait each
+        for (int i = k; i < issued; i++) {
+            const unsigned n = q + i;
+            stage_wait(smem_u32(&bars[n % (unsigned)S]), (n / (unsigned)S) & 1u);
+        }
+    }
+    q += K;
+    return ok;
+}
+
 // The worker of tile w (all NT threads of the CTA); smem_raw holds at least
-// 2 K elements.  Returns when the solve of `a` ends.
+// 2 K elements, then (single-solve FP32 kernel with a staged table) the
+// window slots from byte stage_offset(K).  Returns when the solve of `a`
+// ends.
 //
 // One sub-domain per iteration.  Barriers per iteration: one after the scan
 // (per-warp argmax partials, double-buffered by iteration parity, with the
 // flag / stop state read by thread 0 while it scanned), one after the
 // soft-lock maxima (border candidates only) and one after the window update
 // (accepted candidates only).
-template <typename real, int NT, int RB>
+template <typename real, int NT, int RB, bool STAGED>
 __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char *smem_raw) {
     constexpr int kRowBlock = RB;
+    // the staged window update (FP32 kernels built with it, a table in the
+    // window layout given)
+    const bool staged = STAGED && std::is_same<real, float>::value && a.wtab != nullptr;
+    __shared__ __align__(8) uint64_t s_tbar[kMaxStageSlots];
+    float *ring = reinterpret_cast<float *>(smem_raw + stage_offset(a.K));
+    unsigned q_stage = 0;
     constexpr int NW = NT / 32;
     real *snrm = reinterpret_cast<real *>(smem_raw), *sinv = snrm + a.K;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -321,6 +484,11 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         for (int i = 0; i < 6; i++) s_ph[i] = 0;
         s_cand = 0;
         s_t = clock64();
+        if (staged) {
+            for (int i = 0; i < a.wslots; i++)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_tbar[i])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
     }
     // Dirty sub-domains (tiles of at most 64): a bit is cleared when a scan
     // finds nothing above tol and set again when beta in the sub-domain may
@@ -576,7 +744,12 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                 // beta_k[s] -= C[k][k0][s - s0] dz on V(s0) within the domain
                 const real dz = best.dz;
                 if constexpr (std::is_same<real, float>::value) {
-                    window_v4<NT, kWindowBatch>(a, k0, gi0, gj0, dz);
+                    if (staged) {
+                        if (!window_staged<NT>(a, ring, s_tbar, q_stage, k0, gi0, gj0, dz) && threadIdx.x == 0)
+                            set_stop(a.hdr, CSC_ERR_TIMEOUT);
+                    } else {
+                        window_v4<NT, kWindowBatch>(a, k0, gi0, gj0, dz);
+                    }
                 } else {
                     // the table loads of a unit first, then its reductions
                     const int W0 = a.W0, W1 = a.W1;

@@ -290,3 +290,21 @@ def test_global_tiles_with_more_than_64_subdomains_per_tile(pkg, orc):
     f_ref = orc.objective(X, D, ref["Z"], lam)
     assert abs(orc.objective(X, D, Zh, lam) - f_ref) <= 1e-5 * abs(f_ref)
     assert kkt_fp64_within_bound(orc, X, D, Zh, lam, tol)[0]
+
+
+def test_global_tiles_narrower_than_a_window_are_refused(pkg):
+    """The soft-lock of a global-memory tile tests one strip of V(s0) per
+    dimension, so asynchronous global tiles must be at least 2 L_i - 1 wide;
+    a narrower tile is refused before any launch (the no-lock and automatic
+    plans are unaffected)."""
+    w = ASYNC[3]  # L = 8 x 8
+    X, D, _ = make_problem(w, 38)
+    Xd, Dd = dev(X), dev(D)
+    beta, dtd, lmax = pkg.csc_init_beta(Xd, Dd)
+    with pytest.raises(pkg.CscError) as e:
+        pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, 0.1 * lmax, 1e-4,
+                           opts=pkg.default_opts(placement=2, tile=(14, 46)))
+    assert e.value.status == pkg.CSC_ERR_INVALID
+    Z, st = pkg.csc_lgcd_solve(Xd, Dd, dtd, beta, 0.1 * lmax, 1e-4,
+                               opts=pkg.default_opts(placement=2, tile=(15, 46)))
+    assert st["status"] == pkg.CSC_OK and st["placement"] == 2
