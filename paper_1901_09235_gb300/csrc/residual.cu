@@ -298,6 +298,15 @@ __global__ void __launch_bounds__(NT) gather_beta_kernel(GatherArgs a) {
     const bool live = tr < a.bh && i < a.Z0 && j < a.Z1;
     const long long plane = (long long)a.Z0 * a.Z1;
     const long long at = (long long)i * a.Z1 + j;
+    // ||D_k||^2 and its inverse in FP32, rounded as the LGCD worker rounds
+    // them, once per CTA (an FP64 division per position and atom would make
+    // the FP64 pipe the kernel's bound)
+    __shared__ float s_nk[KMAX], s_ik[KMAX];
+    if (threadIdx.x < a.K && threadIdx.x < KMAX) {
+        const double nk = a.nrm[threadIdx.x];
+        s_nk[threadIdx.x] = (float)nk;
+        s_ik[threadIdx.x] = (float)(1.0 / nk);
+    }
     float acc[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; k++) acc[k] = (live && k < a.K) ? __ldcs(a.beta0 + k * plane + at) : 0.f;
@@ -356,13 +365,13 @@ __global__ void __launch_bounds__(NT) gather_beta_kernel(GatherArgs a) {
         }
     }
     unsigned long long m = 0;
+    __syncthreads();  // s_nk, s_ik
     if (live) {
 #pragma unroll
         for (int k = 0; k < KMAX; k++) {
             if (k >= a.K) break;
             a.beta[k * plane + at] = acc[k];
-            const double nk = a.nrm[k];
-            float dz = coord_update(acc[k], a.lambda, (float)nk, (float)(1.0 / nk)) - __ldcs(a.Z + k * plane + at);
+            float dz = coord_update(acc[k], a.lambda, s_nk[k], s_ik[k]) - __ldcs(a.Z + k * plane + at);
             dz = dz < 0.f ? -dz : dz;
             const unsigned long long b = nonneg_bits(dz);
             m = b > m ? b : m;
