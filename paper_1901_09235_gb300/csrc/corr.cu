@@ -253,19 +253,24 @@ static int corr_rows_dispatch(const Geom &g, CorrArgs<float> a, cudaStream_t st)
         if (g.K <= 10) return run_corr_rows<128, 1, 4, 10, EPI>(g, a, st);
         return run_corr_rows<128, 1, 4, 16, EPI>(g, a, st);
     }
-    // 2-D: 8 rows x 128 columns per CTA of 256 threads (4 positions each);
-    // the atom chunk (8, 13 or 16) that pads K least (25 atoms: two chunks of
-    // 13).  On the 4096^2 image with 25 atoms of 32 x 32: 15.8 ms against
-    // 19.6-19.8 ms for 128 threads x 4 rows, 16.1 for 512 x 16 rows, 16.9 for
-    // 384 x 12 rows, 20.6-21.9 with 8 positions a thread.  Beside a running
+    // 2-D: the atom chunk that pads K least -- 5 atoms x 8 positions a
+    // thread on 24 rows x 128 columns per CTA of 384 threads (72 registers),
+    // else 8, 13 or 16 atoms x 4 positions on 8 rows x 128 columns per CTA of
+    // 256.  On the 4096^2 image with 25 atoms of 32 x 32: 14.5 ms for five
+    // chunks of 5 against 15.8 ms for two of 13 (256 x 8 rows), 15.0 ms for
+    // 5 atoms on 256 x 16 rows, 14.6 on 384 x 12 or 48 rows, 16.2-16.9 on 320,
+    // 448 or 512 threads, 19.6-19.8 for 128 threads x 4 rows.  Beside a running
     // queue kernel only one warp of 128 registers fits per SM sub-partition:
     // 128 threads x 4 rows then.
-    const long long w13 = ceil_div(g.K, 13) * 13, w16 = ceil_div(g.K, 16) * 16;
+    const long long w5 = ceil_div(g.K, 5) * 5, w13 = ceil_div(g.K, 13) * 13, w16 = ceil_div(g.K, 16) * 16;
     if (live_queues() > 0) {
         if (g.K <= 8) return run_corr_rows<128, 4, 4, 8, EPI>(g, a, st);
         if (w13 < w16) return run_corr_rows<128, 4, 4, 13, EPI>(g, a, st);
         return run_corr_rows<128, 4, 4, 16, EPI>(g, a, st);
     }
+    // chunks of 5 cost about 12/13 as much per atom as the others
+    const long long wmin = std::min<long long>(g.K <= 8 ? 8 : w13, w16);
+    if (12 * w5 <= 13 * wmin) return run_corr_rows<384, 24, 8, 5, EPI>(g, a, st);
     if (g.K <= 8) return run_corr_rows<256, 8, 4, 8, EPI>(g, a, st);
     if (w13 < w16) return run_corr_rows<256, 8, 4, 13, EPI>(g, a, st);
     return run_corr_rows<256, 8, 4, 16, EPI>(g, a, st);
@@ -420,6 +425,7 @@ int preload_corr_kernels() {
         (const void *)corr_rows_kernel<256, 8, 4, 8, EPI_INIT>,
         (const void *)corr_rows_kernel<256, 8, 4, 13, EPI_INIT>,
         (const void *)corr_rows_kernel<256, 8, 4, 16, EPI_INIT>,
+        (const void *)corr_rows_kernel<384, 24, 8, 5, EPI_INIT>,
         (const void *)corr_rows_kernel<128, 1, 4, 4, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 1, 4, 8, EPI_REFRESH>,
         (const void *)corr_rows_kernel<128, 1, 4, 10, EPI_REFRESH>,
@@ -430,6 +436,7 @@ int preload_corr_kernels() {
         (const void *)corr_rows_kernel<256, 8, 4, 8, EPI_REFRESH>,
         (const void *)corr_rows_kernel<256, 8, 4, 13, EPI_REFRESH>,
         (const void *)corr_rows_kernel<256, 8, 4, 16, EPI_REFRESH>,
+        (const void *)corr_rows_kernel<384, 24, 8, 5, EPI_REFRESH>,
         (const void *)dtd_kernel<float, 256>,
         (const void *)atom_norm_kernel<float, 256>,
     };
