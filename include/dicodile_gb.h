@@ -415,6 +415,21 @@ CSC_API int csc_lgcd_solve_f64(const csc_shape *shape, const double *X, const do
 CSC_API int cdl_dict_stats_noalloc(const csc_shape *shape, const float *Z, const float *X, float *phi,
                                    float *psi, csc_stream_t stream);
 
+/* The sparse code: the nonzeros of Z (the activations of Eq. csc) as a list
+ * in (position, atom) order -- positions ascending, atoms ascending within a
+ * position.  Entry i is atom k_out[i], position s_out[i] in atom k's plane
+ * (i0 * Z1 + i1 in 2-D, the time index in 1-D) and value val_out[i].
+ *   Z: device, K x Z0 x Z1 FP32.  k_out, s_out, val_out: device arrays of cap
+ *   entries owned by the caller (may be NULL when cap = 0).  nnz_out: host,
+ *   receives the number of nonzeros.  workspace: at least
+ *   csc_workspace_size bytes (block counts and the header).
+ * Synchronises `stream` once to read the count.  Returns CSC_ERR_WORKSPACE,
+ * with *nnz_out set and nothing written, when the count exceeds cap (call
+ * again with a larger cap, or with cap = 0 to count only). */
+CSC_API int csc_sparse_code(const csc_shape *shape, const float *Z, int *k_out, int *s_out, float *val_out,
+                            long long cap, long long *nnz_out, void *workspace, size_t workspace_bytes,
+                            csc_stream_t stream);
+
 /* Human-readable name of a status code (static storage). */
 CSC_API const char *csc_status_string(int status);
 

@@ -98,6 +98,7 @@ def load():
         "csc_lgcd_solve_f64": (i, [S, p, p, p, p, p, d, d, O, p, sz, ST, p]),
         "csc_objective": (i, [S, p, p, p, d, C.POINTER(d), p, sz, p]),
         "cdl_dict_stats": (i, [S, p, p, p, p, p, sz, p]),
+        "csc_sparse_code": (i, [S, p, p, p, p, C.c_longlong, C.POINTER(C.c_longlong), p, sz, p]),
         "cdl_dict_update": (i, [S, p, p, d, p, i, d, C.POINTER(d), C.POINTER(i), p, sz, p]),
         "cdl_fit": (i, [S, p, p, p, p, p, p, p, d, d, i, d, i, d, O, p, sz, C.POINTER(d), C.POINTER(i), p]),
         "cdl_step": (i, [S, p, p, p, p, p, p, p, d, d, d, d, i, d, O, p, sz, ST, C.POINTER(d), C.POINTER(d),
@@ -480,6 +481,37 @@ def cdl_dict_stats(Z, X, D_shape, phi=None, psi=None, ws=None, stream=None):
     _check(load().cdl_dict_stats(C.byref(s), _ptr(Z), _ptr(X), _ptr(phi), _ptr(psi), _ptr(ws),
                                  ws.numel(), _stream(stream)), "cdl_dict_stats")
     return phi, psi
+
+
+def sparse_code(Z, X_shape, D_shape, out=None, ws=None, stream=None):
+    """The nonzeros of Z in (position, atom) order (csc_sparse_code): returns
+    (k, s, values, nnz) with k, s int32 and values float32 device tensors of
+    nnz entries (views of `out`, a (k, s, values) triple of capacity cap, when
+    given; when the count exceeds cap, a CscError with the count in .stats)."""
+    import torch
+    _need(Z, torch.float32, "Z")
+    s = make_shape(tuple(X_shape), tuple(D_shape))
+    if ws is None:
+        ws = workspace(s, device=Z.device)
+    n = C.c_longlong(0)
+    lib = load()
+    if out is None:
+        rc = lib.csc_sparse_code(C.byref(s), _ptr(Z), None, None, None, 0, C.byref(n), _ptr(ws), ws.numel(),
+                                 _stream(stream))
+        if rc not in (CSC_OK, CSC_ERR_WORKSPACE):
+            _check(rc, "csc_sparse_code")
+        cap = max(1, n.value)
+        out = (torch.empty(cap, dtype=torch.int32, device=Z.device),
+               torch.empty(cap, dtype=torch.int32, device=Z.device),
+               torch.empty(cap, dtype=torch.float32, device=Z.device))
+    kb, sb, vb = out
+    cap = min(kb.numel(), sb.numel(), vb.numel())
+    rc = lib.csc_sparse_code(C.byref(s), _ptr(Z), _ptr(kb), _ptr(sb), _ptr(vb), cap, C.byref(n), _ptr(ws),
+                             ws.numel(), _stream(stream))
+    if rc != CSC_OK:
+        raise CscError(rc, "csc_sparse_code", {"nnz": n.value, "cap": cap})
+    m = n.value
+    return kb[:m], sb[:m], vb[:m], m
 
 
 def cdl_dict_update(phi, psi, x_sqnorm: float, D, X_shape, max_iter: int = 50, tol: float = 1e-8,

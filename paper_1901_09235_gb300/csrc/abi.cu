@@ -268,6 +268,18 @@ int cdl_dict_update(const csc_shape *shape, const float *phi, const float *psi, 
                             static_cast<unsigned char *>(ws), L, (cudaStream_t)stream);
 }
 
+int csc_sparse_code(const csc_shape *shape, const float *Z, int *k_out, int *s_out, float *val_out,
+                    long long cap, long long *nnz_out, void *ws, size_t ws_bytes, csc_stream_t stream) {
+    Geom g;
+    int rc = make_geom(shape, &g);
+    if (rc) return rc;
+    if (!Z || !nnz_out || !ws || cap < 0 || (cap > 0 && (!k_out || !s_out || !val_out))) return CSC_ERR_INVALID;
+    WsLayout L = plan_workspace(g, 0, 4);
+    if (ws_bytes < L.total) return CSC_ERR_WORKSPACE;
+    return sparse_code_impl(g, Z, k_out, s_out, val_out, cap, nnz_out, static_cast<unsigned char *>(ws), L,
+                            (cudaStream_t)stream);
+}
+
 const char *csc_status_string(int s) {
     switch (s) {
         case CSC_OK: return "ok";

@@ -255,6 +255,29 @@ int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, f
     return stats_launch(g, Z, X, phi, psi, ws, L, st, true);
 }
 
+int sparse_code_impl(const Geom &g, const float *Z, int *k_out, int *s_out, float *val_out, long long cap,
+                     long long *nnz_out, unsigned char *ws, const WsLayout &L, cudaStream_t st) {
+    WsHeader *h = reinterpret_cast<WsHeader *>(ws + L.hdr);
+    int *blk_cnt = reinterpret_cast<int *>(ws + L.blk);
+    int *blk_off = blk_cnt + L.blk_cap;
+    const long long zpos = g.nzpos();
+    const int nblk = (int)ceil_div(zpos, 256);
+    if (nblk > L.blk_cap) return CSC_ERR_WORKSPACE;
+    nz_count_kernel<256><<<nblk, 256, 0, st>>>(Z, zpos, g.K, blk_cnt);
+    nz_scan_kernel<1024><<<1, 1024, 0, st>>>(blk_cnt, blk_off, nblk, h);
+    CSC_CUDA(cudaGetLastError());
+    int t = 0;
+    const int rb_ = read_back(&t, &h->scan_total, st);
+    if (rb_) return rb_;
+    *nnz_out = t;
+    if (t > cap) return CSC_ERR_WORKSPACE;
+    if (t > 0) {
+        nz_write_kernel<256><<<nblk, 256, 0, st>>>(Z, zpos, g.K, blk_off, h, cap, k_out, s_out, val_out);
+        CSC_CUDA(cudaGetLastError());
+    }
+    return CSC_OK;
+}
+
 int dict_stats_deferred(const Geom &g, const float *Z, const float *X, float *phi, float *psi,
                         unsigned char *ws, const WsLayout &L, cudaStream_t st) {
     return stats_launch(g, Z, X, phi, psi, ws, L, st, false);
