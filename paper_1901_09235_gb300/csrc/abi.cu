@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "dict.cuh"
 
 namespace csc {
 

@@ -292,10 +292,6 @@ int solve_impl(const csc_shape *shape, const real *X, const real *D, const real 
 
 int dict_stats_impl(const Geom &g, const float *Z, const float *X, float *phi, float *psi,
                     unsigned char *ws, const WsLayout &L, cudaStream_t st);
-// The nonzeros of Z in (position, atom) order into caller arrays of cap
-// entries; *nnz_out = their number (read back: one synchronisation).
-int sparse_code_impl(const Geom &g, const float *Z, int *k_out, int *s_out, float *val_out, long long cap,
-                     long long *nnz_out, unsigned char *ws, const WsLayout &L, cudaStream_t st);
 // x_sqnorm_dev (optional): ||X||^2 in device memory, read by the kernel in
 // place of x_sqnorm.  gate (optional): when *gate > gate_cap at run time the
 // step leaves D unchanged (statistics that were not computed).
