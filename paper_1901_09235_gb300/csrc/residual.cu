@@ -310,6 +310,10 @@ __global__ void __launch_bounds__(NT) gather_beta_kernel(GatherArgs a) {
     float acc[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; k++) acc[k] = (live && k < a.K) ? __ldcs(a.beta0 + k * plane + at) : 0.f;
+    // the nonzeros of Z at this position, seen among the staged ones (up to two)
+    int zk0 = -1, zk1 = -1;
+    float zv0 = 0.f, zv1 = 0.f;
+    bool zmany = false;
     // bins within L_i - 1 of the tile; the bins of one bin row are contiguous
     // in the list.  Up to 32 bin rows at a time: their ranges are read in one
     // go, then every staged nonzero in one pass.
@@ -351,7 +355,13 @@ __global__ void __launch_bounds__(NT) gather_beta_kernel(GatherArgs a) {
                 // C_t[k'][delta][0..K): the K coefficients of the term, contiguous
                 const float4 *row = reinterpret_cast<const float4 *>(
                     a.ct + ((size_t)(e.x * a.W0 + di + a.L0 - 1) * a.W1 + dj + a.L1 - 1) * a.Kp);
-                const int self = (di == 0 && dj == 0) ? e.x : -1;  // the term of (k, s) itself is left out
+                // the term of (k, s) itself is left out; its z is Z at this position
+                const int self = (di == 0 && dj == 0) ? e.x : -1;
+                if (self >= 0) {
+                    if (zk0 < 0) zk0 = self, zv0 = z;
+                    else if (zk1 < 0) zk1 = self, zv1 = z;
+                    else zmany = true;
+                }
 #pragma unroll
                 for (int g = 0; g < KMAX / 4; g++) {
                     if (4 * g >= a.K) break;
@@ -371,7 +381,10 @@ __global__ void __launch_bounds__(NT) gather_beta_kernel(GatherArgs a) {
         for (int k = 0; k < KMAX; k++) {
             if (k >= a.K) break;
             a.beta[k * plane + at] = acc[k];
-            float dz = coord_update(acc[k], a.lambda, s_nk[k], s_ik[k]) - __ldcs(a.Z + k * plane + at);
+            // Z here: from the staged nonzeros (a position with more than two
+            // nonzero atoms reads Z itself)
+            const float zk = zmany ? __ldcs(a.Z + k * plane + at) : (k == zk0 ? zv0 : (k == zk1 ? zv1 : 0.f));
+            float dz = coord_update(acc[k], a.lambda, s_nk[k], s_ik[k]) - zk;
             dz = dz < 0.f ? -dz : dz;
             const unsigned long long b = nonneg_bits(dz);
             m = b > m ? b : m;
