@@ -621,29 +621,6 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
         const bool active = best.a >= a.eps;
         bool accepted = false;
         int li0 = 0, lj0 = 0;
-        if (!STAGED && use_mask) {
-            // pull the next dirty sub-domain's beta and Z rows into L2 while
-            // this iteration's soft-lock and window update run (one line per
-            // row start; rows of a sub-domain span at most a few lines).  The
-            // single-solve kernel leaves it out: on the 4096^2 image its solve
-            // took 37.6 ms with these prefetches and 36.6 ms without.
-            const unsigned long long rest = (active ? dmask : dmask & ~(1ull << m));
-            const unsigned long long above = m + 1 < 64 ? (rest >> (m + 1)) << (m + 1) : 0ull;
-            const int mn = above ? __ffsll((long long)above) - 1 : (rest ? __ffsll((long long)rest) - 1 : -1);
-            if (mn >= 0 && mn != m) {
-                const int nr = mn / ns1, nc = mn - nr * ns1;
-                const int pr0 = nr * a.sub0, pc0 = nc * a.sub1;
-                const int pbh = min(a.sub0, h - pr0), pbw = min(a.sub1, wd - pc0);
-                const int lines = (pbw + 31) >> 5;  // 128-byte lines per row, at most
-                for (int q = threadIdx.x; q < K * pbh * lines; q += NT) {
-                    const int k = q / (pbh * lines), rem = q - k * (pbh * lines), rr = rem / lines;
-                    const int cc = (rem - rr * lines) * 32;
-                    const size_t g = (size_t)k * plane + (size_t)(or0 + pr0 + rr) * a.Z1 + oc0 + pc0 + cc;
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.beta + g));
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Z + g));
-                }
-            }
-        }
         if (active) {
             const unsigned pos = best.key / (unsigned)K;
             const int k0 = (int)(best.key - pos * (unsigned)K);
