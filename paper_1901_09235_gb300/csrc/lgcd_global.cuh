@@ -260,6 +260,76 @@ __device__ __forceinline__ void window_v4(const LgcdArgs<float> &a, int k0, int 
     }
 }
 
+// ------------------------------------------------------------ soft-lock
+// The part of V(s0) outside the tile as strip A = rows outside the tile rows
+// (full width of V, nA rows from ra0, wA columns from u0) and strip B = tile
+// rows, columns outside the tile columns (nB rows from rb0, wB columns from
+// cb0).
+struct SoftlockStrips {
+    int ra0, nA, u0, wA, rb0, nB, cb0, wB;
+};
+template <typename real>
+struct Pair {
+    real x, y;
+};
+
+// This warp's maxima of |dZ| over the coordinates of both strips held by
+// lower-ranked (x) and higher-ranked (y) tiles, in units of (atom, block of RB
+// rows, 32-column chunk); a warp stops once any warp of the CTA found a
+// blocker of the candidate's |dZ| ba (Eq. soft_lock: it loses to a
+// lower-ranked tile on a tie, to a higher-ranked one only when strictly
+// smaller).  Out of line, so that its registers do not weigh on the rest of
+// the worker (inlined, its spills cost up to 40 % of the phase).
+template <typename real, int NT, int RB>
+__device__ __noinline__ Pair<real> softlock_maxima(const real *beta, const real *Zg, const real *snrm,
+                                                   const real *sinv, real lambda, int K, int Z1, size_t plane, int G1,
+                                                   int w, int ta, int tb, int or0, int oc0, int h, int wd,
+                                                   SoftlockStrips sl, real ba, volatile int *s_block) {
+    constexpr int NW = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    real lo = real(-1), hi = real(-1);
+    const int nchA = (sl.wA + 31) >> 5, nchB = (sl.wB + 31) >> 5;
+    const int unA = ((sl.nA + RB - 1) / RB) * nchA;
+    const int per_k = unA + ((sl.nB + RB - 1) / RB) * nchB;
+    for (int u = warp; u < K * per_k; u += NW) {
+        if (*s_block) break;  // another warp already rejects the candidate
+        const int k = u / per_k, rem = u - k * per_k;
+        const bool inA = rem < unA;
+        const int nchS = inA ? nchA : nchB, remS = inA ? rem : rem - unA;
+        const int rb = remS / nchS, ch = remS - rb * nchS;
+        const int cc = ch * 32 + lane;
+        const int gi = (inA ? sl.ra0 : sl.rb0) + rb * RB, gj = (inA ? sl.u0 : sl.cb0) + cc;
+        const int nrow = cc < (inA ? sl.wA : sl.wB) ? min(RB, (inA ? sl.nA : sl.nB) - rb * RB) : 0;
+        const real *bk = beta + (size_t)k * plane, *zk = Zg + (size_t)k * plane;
+        const int o0 = gi * Z1 + gj;
+        real bv[RB], zv[RB];
+#pragma unroll
+        for (int q = 0; q < RB; q++) {
+            if (q < nrow) {
+                bv[q] = ld_relaxed(bk + (o0 + q * Z1));
+                zv[q] = ld_relaxed(zk + (o0 + q * Z1));
+            }
+        }
+        // rank of the tile holding (gi + q, gj): neighbours of a tile are at
+        // most one tile away in each direction
+        const int tj = gj < oc0 ? tb - 1 : (gj >= oc0 + wd ? tb + 1 : tb);
+        const real nk = snrm[k], ik = sinv[k];
+#pragma unroll
+        for (int q = 0; q < RB; q++) {
+            if (q < nrow) {
+                real d = coord_update(bv[q], lambda, nk, ik) - zv[q];
+                d = d < real(0) ? -d : d;
+                const int gq = gi + q;
+                const int ti = gq < or0 ? ta - 1 : (gq >= or0 + h ? ta + 1 : ta);
+                if (ti * G1 + tj < w) lo = max(lo, d);
+                else hi = max(hi, d);
+            }
+        }
+        if (__any_sync(0xffffffffu, lo >= ba || hi > ba) && lane == 0) *s_block = 1;
+    }
+    return Pair<real>{lo, hi};
+}
+
 // ------------------------------------------------ staged window update
 // The single-solve FP32 kernel stages the K blocks C[k][k0] (k = 0..K-1) of
 // an update in shared memory: a ring of a.wslots slots, each filled by one
@@ -640,48 +710,11 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
                 const int cb0 = u0 < oc0 ? u0 : max(u0, oc0 + wd), cb1 = u0 < oc0 ? min(u1, oc0) : u1;
                 const int nA = max(0, ra1 - ra0), nB = (cb1 > cb0) ? max(0, rb1 - rb0) : 0;
                 const int wA = u1 - u0, wB = max(0, cb1 - cb0);
-                real lo = real(-1), hi = real(-1);
-                const int nchA = (wA + 31) >> 5, nchB = (wB + 31) >> 5;
-                const int unA = ((nA + kRowBlock - 1) / kRowBlock) * nchA;
-                const int per_k = unA + ((nB + kRowBlock - 1) / kRowBlock) * nchB;
-                for (int u = warp; u < K * per_k; u += NW) {
-                    if (s_block) break;  // another warp already rejects best
-                    const int k = u / per_k, rem = u - k * per_k;
-                    const bool inA = rem < unA;
-                    const int nchS = inA ? nchA : nchB, remS = inA ? rem : rem - unA;
-                    const int rb = remS / nchS, ch = remS - rb * nchS;
-                    const int cc = ch * 32 + lane;
-                    const int gi = (inA ? ra0 : rb0) + rb * kRowBlock, gj = (inA ? u0 : cb0) + cc;
-                    const int nrow = cc < (inA ? wA : wB) ? min(kRowBlock, (inA ? nA : nB) - rb * kRowBlock) : 0;
-                    const real *bk = a.beta + (size_t)k * plane, *zk = a.Z + (size_t)k * plane;
-                    const int o0 = gi * a.Z1 + gj;
-                    real bv[kRowBlock], zv[kRowBlock];
-#pragma unroll
-                    for (int q = 0; q < kRowBlock; q++) {
-                        if (q < nrow) {
-                            bv[q] = ld_relaxed(bk + (o0 + q * a.Z1));
-                            zv[q] = ld_relaxed(zk + (o0 + q * a.Z1));
-                        }
-                    }
-                    // rank of the tile holding (gi + q, gj): neighbours of a
-                    // tile are at most one tile away in each direction
-                    const int tj = gj < oc0 ? tb - 1 : (gj >= oc0 + wd ? tb + 1 : tb);
-                    const real nk = snrm[k], ik = sinv[k];
-#pragma unroll
-                    for (int q = 0; q < kRowBlock; q++) {
-                        if (q < nrow) {
-                            real d = coord_update(bv[q], a.lambda, nk, ik) - zv[q];
-                            d = d < real(0) ? -d : d;
-                            const int gq = gi + q;
-                            const int ti = gq < or0 ? ta - 1 : (gq >= or0 + h ? ta + 1 : ta);
-                            if (ti * a.G1 + tj < w) lo = max(lo, d);
-                            else hi = max(hi, d);
-                        }
-                    }
-                    // a blocker: best loses to a lower-ranked tile on a tie,
-                    // to a higher-ranked one only when strictly smaller
-                    if (__any_sync(0xffffffffu, lo >= best.a || hi > best.a) && lane == 0) s_block = 1;
-                }
+                const SoftlockStrips sl{ra0, nA, u0, wA, rb0, nB, cb0, wB};
+                const Pair<real> lh = softlock_maxima<real, NT, kRowBlock>(
+                    a.beta, a.Z, snrm, sinv, a.lambda, K, a.Z1, plane, a.G1, w, ta, tb, or0, oc0, h, wd, sl, best.a,
+                    &s_block);
+                real lo = lh.x, hi = lh.y;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
