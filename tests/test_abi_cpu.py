@@ -89,6 +89,31 @@ def test_null_pointers_rejected(lib):
     assert lib.cdl_dict_stats(C.byref(s), None, None, None, None, None, 0, None) == pkg.CSC_ERR_INVALID
 
 
+def test_sparse_code_arguments_rejected_on_host(lib):
+    """csc_sparse_code validates its pointers, capacity and workspace size
+    before any device work."""
+    import paper_1901_09235_gb300 as pkg
+    s = pkg.make_shape((1, 64, 64), (5, 1, 8, 8))
+    n = C.c_longlong(-1)
+    fake = C.c_void_p(0x1000)  # never dereferenced: every case fails on the host
+    ws_need = pkg.workspace_size(s)
+
+    def call(Z=fake, k=fake, sv=fake, v=fake, cap=16, nnz=True, ws=fake, ws_bytes=ws_need):
+        return lib.csc_sparse_code(C.byref(s), Z, k, sv, v, cap, C.byref(n) if nnz else None, ws, ws_bytes, None)
+
+    assert call(Z=None) == pkg.CSC_ERR_INVALID
+    assert call(nnz=False) == pkg.CSC_ERR_INVALID
+    assert call(ws=None) == pkg.CSC_ERR_INVALID
+    assert call(cap=-1) == pkg.CSC_ERR_INVALID
+    for missing in ("k", "sv", "v"):
+        assert call(**{missing: None}) == pkg.CSC_ERR_INVALID, missing
+    assert call(ws_bytes=1024) == pkg.CSC_ERR_WORKSPACE
+    bad = pkg.make_shape((1, 64, 64), (5, 1, 8, 8))
+    bad.K = 0
+    assert lib.csc_sparse_code(C.byref(bad), fake, fake, fake, fake, 16, C.byref(n), fake, ws_need,
+                               None) == pkg.CSC_ERR_INVALID
+
+
 def test_option_and_queue_arguments_rejected_on_host(lib):
     """Out-of-range solve options and queue densities are refused before any
     device work (the pointers below are never dereferenced)."""
