@@ -48,6 +48,32 @@ def test_soft_locks_terminate_at_the_oracle_optimum(orc, w, tile, schedule, seed
     assert abs(pb.objective(sim.Z) - f_ref) <= 1e-9 * f_ref
 
 
+SUB_CASES = [(W2, (16, 16), (4, 4), "random", 4, 50), (W2, (12, 20), (4, 4), "lockstep", 0, 1),
+             (W1, (32,), (8,), "random", 5, 50)]
+
+
+@pytest.mark.parametrize("w,tile,sub,schedule,seed,delay", SUB_CASES,
+                         ids=[f"{c[0].name}-{'x'.join(map(str, c[1]))}-sub{'x'.join(map(str, c[2]))}-{c[3]}{c[4]}"
+                              for c in SUB_CASES])
+def test_direction_marking_with_many_sub_domains(orc, w, tile, sub, schedule, seed, delay):
+    """Sub-domains of side L inside tiles of several of them, as the GPU
+    runs (4096^2 image: 32 x 32 sub-domains of 255 x 214 tiles): a bump from
+    a neighbour marks only the receiver's sub-domains facing it, and the run
+    still ends at the oracle's optimum with max |dZ| < eps."""
+    X, D, _ = make_problem(w, 2)
+    lam = 0.1 * orc.lambda_max(X, D)
+    pb = Problem(X, D, lam, EPS)
+    sim = Sim(pb, tile=tile, sub=sub, lock=True, schedule=schedule, seed=seed, max_delay=delay)
+    sim.run()
+    assert sim.stop is None
+    assert sim.pending == 0 and not sim.in_flight and sim.G >= 4
+    assert sim.accepted > 0
+    assert pb.kkt(sim.Z) < EPS * (1 + 1e-9)
+    ref = orc.lgcd(X, D, lam, EPS)
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    assert abs(pb.objective(sim.Z) - f_ref) <= 1e-9 * f_ref
+
+
 def _corner_problem():
     """One 4 x 4 box atom; activations of 5 at every tile corner of a 4 x 4
     tile grid, so the four tiles around a corner all find their best
