@@ -1012,9 +1012,12 @@ def large_image_main(args):
 
 
 def launches_per_step_solve(st):
-    # init_beta: corr + dtd; solve: atom norms + per round (ctl memset, header
-    # reset, LGCD, 7 refresh kernels)
-    return 2 + 1 + 9 * int(st["refresh_rounds"])
+    # init_beta: correlation + DtD table; solve: atom norms + window-layout
+    # table, then per round: header reset, LGCD, and the refresh (reset,
+    # nonzero list, residual init / scatter / finish, dense check, transposed
+    # table, bin count / scan / fill, gather, the gated correlation refresh)
+    # -- 18 kernels for a one-round solve, as the ncu launch list shows
+    return 2 + 2 + 14 * int(st["refresh_rounds"])
 
 
 # ------------------------------------------------ full CDL on the 8192^2 image
