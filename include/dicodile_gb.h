@@ -162,6 +162,13 @@ CSC_API int csc_init_beta(const csc_shape *shape, const float *X, const float *D
  *              by tol or more; this is then re-checked on a fresh beta
  *              (stats->max_dz_final) and the solve resumes if it fails.
  *   stats    : host pointer, may be NULL.
+ *   workspace: csc_workspace_size() bytes.  FP32 solves on tiles in global
+ *              memory use its tail for the initial beta (the final beta is
+ *              rebuilt from it and the nonzeros of Z), the table laid out for
+ *              the staged window update and the bins of that rebuild; with
+ *              less (but at least the required head) they recompute beta by
+ *              correlation and read the table from L2 instead.  Such solves
+ *              also need beta and Z on 16-byte boundaries (CSC_ERR_INVALID).
  * Synchronises `stream` before returning (the status comes from the device). */
 CSC_API int csc_lgcd_solve(const csc_shape *shape, const float *X, const float *D, const float *dtd,
                    float *beta, float *Z, float lambda, float tol, const csc_solve_opts *opts,
