@@ -6,6 +6,8 @@
 // compacted nonzeros of Z with FP64 atomics: every nonzero (k, s, z) adds
 // -z D_k to the residual on s + Theta.  If the nonzeros do not fit the list
 // the residual is rebuilt densely instead.
+#include <cstdint>
+
 #include "lgcd_global.cuh"
 
 namespace csc {
@@ -13,6 +15,67 @@ namespace csc {
 // Nonzeros of Z into (k, s, z) lists; order is unspecified (one atomic per
 // warp).  Counts past the capacity only set the overflow flag.  The same
 // pass accumulates ||Z||_1 in FP64.
+// The same for FP32 Z on a 16-byte boundary: each thread reads four entries
+// with one 16-byte load; a warp reserves its nonzeros with one atomic and
+// places them by a prefix sum of the per-thread counts.
+template <int NT>
+__global__ void __launch_bounds__(NT) compact_v4_kernel(const float *Z, long long zpos, int K, int *nk, int *ns,
+                                                       float *nzv, long long cap, WsHeader *h) {
+    const long long n = (long long)K * zpos, n4 = n / 4, groups = (n + 3) / 4;
+    const int lane = threadIdx.x & 31;
+    double l1 = 0.0;
+    const float4 *Z4 = reinterpret_cast<const float4 *>(Z);
+    // the loop bound is the same for every thread of the block (warp-wide
+    // shuffles below); threads past the end hold no entries
+    for (long long base = (long long)blockIdx.x * NT; base < groups; base += (long long)gridDim.x * NT) {
+        const long long g = base + threadIdx.x, i0 = 4 * g;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (g < n4) {
+            const float4 w = __ldcs(Z4 + g);
+            v[0] = w.x;
+            v[1] = w.y;
+            v[2] = w.z;
+            v[3] = w.w;
+        } else if (g < groups) {  // the last n mod 4 entries
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (i0 + e < n) v[e] = Z[i0 + e];
+        }
+        unsigned m4 = 0;
+#pragma unroll
+        for (int e = 0; e < 4; e++) m4 |= (v[e] != 0.f ? 1u : 0u) << e;
+        const int c = __popc(m4);
+        int x = c;  // inclusive prefix of the counts over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, x, 31);
+        if (total == 0) continue;
+        unsigned long long wbase = 0;
+        if (lane == 0) wbase = atomicAdd((unsigned long long *)&h->nnz, (unsigned long long)total);
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        long long idx = (long long)wbase + x - c;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            if (m4 >> e & 1u) {
+                l1 += fabs((double)v[e]);
+                const long long i = i0 + e;
+                if (idx < cap) {
+                    nk[idx] = (int)(i / zpos);
+                    ns[idx] = (int)(i % zpos);
+                    nzv[idx] = v[e];
+                } else {
+                    h->overflow = 1;
+                }
+                idx++;
+            }
+        }
+    }
+    block_sum_atomic<NT>(l1, &h->obj_g);
+}
+
 template <typename real, int NT>
 __global__ void __launch_bounds__(NT) compact_any_kernel(const real *Z, long long zpos, int K,
                                                          int *nk, int *ns, real *nzv, long long cap,
@@ -407,8 +470,16 @@ int launch_refresh(const Geom &g, const WsLayout &L, unsigned char *ws, const re
     const long long nx = g.nx(), nz = g.nz();
 
     refresh_reset_kernel<<<1, 1, 0, st>>>(h);
-    compact_any_kernel<real, 256><<<grid_for(nz, 256), 256, 0, st>>>(Z, g.nzpos(), g.K, nk, ns, nzv,
-                                                                      L.nnz_cap, h);
+    bool v4 = false;
+    if constexpr (sizeof(real) == 4) v4 = (reinterpret_cast<uintptr_t>(Z) & 15) == 0;
+    if (v4) {
+        if constexpr (sizeof(real) == 4)
+            compact_v4_kernel<256><<<grid_for((nz + 3) / 4, 256), 256, 0, st>>>(Z, g.nzpos(), g.K, nk, ns, nzv,
+                                                                                 L.nnz_cap, h);
+    } else {
+        compact_any_kernel<real, 256><<<grid_for(nz, 256), 256, 0, st>>>(Z, g.nzpos(), g.K, nk, ns, nzv,
+                                                                          L.nnz_cap, h);
+    }
     residual_init_kernel<real><<<grid_for(nx, 256), 256, 0, st>>>(X, R, nx);
     scatter_kernel<real, 128><<<152 * 8, 128, 0, st>>>(nk, ns, nzv, h, L.nnz_cap, D, R, g.P, g.L0,
                                                        g.L1, g.T0, g.T1, g.Z1);
@@ -472,6 +543,7 @@ int preload_residual_kernels() {
     const void *fns[] = {
         (const void *)refresh_reset_kernel,
         (const void *)compact_any_kernel<float, 256>,
+        (const void *)compact_v4_kernel<256>,
         (const void *)residual_init_kernel<float>,
         (const void *)scatter_kernel<float, 128>,
         (const void *)recon_dense_kernel<float>,
