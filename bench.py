@@ -223,16 +223,31 @@ def lgcd_algorithmic_bytes(st, w):
     return 8 * st["candidates"] + st["updates"] * (12 * w.K * win + 4)
 
 
+def source_digest(paths):
+    """SHA-256 of kernel sources with comments and blank lines taken out, so
+    that a committed ncu summary stays tied to the code it measured and not
+    to the wording of its comments."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in paths:
+        text = open(f).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
+    return h.hexdigest()
+
+
 def lgcd_traffic_per_launch():
     """DRAM bytes per LGCD launch from the committed ncu summary, or None when
     the kernel sources changed since those counters were taken."""
-    import hashlib
     prof = os.path.join(ROOT, "profiles", "lgcd_async_kernel_csc1d_T200000_P5_K10_L64.md")
     src = [os.path.join(ROOT, "paper_1901_09235_gb300", "csrc", f)
            for f in ("lgcd_async.cu", "lgcd_common.cuh", "common.cuh")]
     try:
         text = open(prof).read()
-        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()
+        h = source_digest(src)
     except OSError:
         return None
     vals = dict(line.split(" = ", 1) for line in text.splitlines() if " = " in line)
@@ -759,12 +774,11 @@ def image_algorithmic_bytes(st, w):
 def profile_value(name, key, sources):
     """A value recorded in a committed ncu summary under profiles/, or None
     when the kernel sources changed since it was taken."""
-    import hashlib
     prof = os.path.join(ROOT, "profiles", name)
     src = [os.path.join(ROOT, "paper_1901_09235_gb300", "csrc", f) for f in sources]
     try:
         text = open(prof).read()
-        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()
+        h = source_digest(src)
     except OSError:
         return None
     vals = dict(line.split(" = ", 1) for line in text.splitlines() if " = " in line)

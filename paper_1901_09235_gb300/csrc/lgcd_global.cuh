@@ -20,8 +20,8 @@ namespace csc {
 // neighbour learns that its beta changed through its notification counters
 // (one per neighbour direction): a worker bumps, in every tile V(s0) reaches,
 // the counter of the direction it lies in.  The counters carry the same termination accounting as the mailboxes of the
-// shared-memory variant: `pending` counts active workers plus flag bumps not
-// yet observed by their tile.  One sub-domain per iteration, scanned and
+// shared-memory variant: `pending` counts active workers plus counter bumps
+// not yet observed by their tile.  One sub-domain per iteration, scanned and
 // updated by the whole CTA.
 // Threads per worker CTA of the single-solve kernel (two CTAs per SM).
 // Measured on the 4096^2 image (25 atoms of 32 x 32): 456 x 256, 608 x 256
@@ -490,9 +490,10 @@ __device__ bool window_staged(const LgcdArgs<float> &a, float *ring, uint64_t *b
 //
 // One sub-domain per iteration.  Barriers per iteration: one after the scan
 // (per-warp argmax partials, double-buffered by iteration parity, with the
-// flag / stop state read by thread 0 while it scanned), one after the
-// soft-lock maxima (border candidates only) and one after the window update
-// (accepted candidates only).
+// notification counters and the stop word read by warp 0 while it scanned),
+// one after the soft-lock maxima (border candidates only) and one after the
+// window update (accepted candidates only; the staged update adds one per
+// table block).
 template <typename real, int NT, int RB, bool STAGED>
 __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char *smem_raw) {
     constexpr int kRowBlock = RB;
@@ -563,7 +564,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
     // Dirty sub-domains (tiles of at most 64): a bit is cleared when a scan
     // finds nothing above tol and set again when beta in the sub-domain may
     // have changed -- an accepted update whose window V(s0) reaches it, or a
-    // neighbour's flag bump for those along the border band.  The worker
+    // neighbour's notification for those facing that neighbour.  The worker
     // pauses once no sub-domain is dirty.  Larger tiles scan cyclically and
     // pause after M quiet iterations.
     const bool use_mask = M <= 64;
@@ -847,7 +848,7 @@ __device__ void global_tile_worker(const LgcdArgs<real> &a, int w, unsigned char
             pause = quiet >= M;
         }
         if (pause) {
-            // pause until a neighbour bumps the flag or every worker is done
+            // pause until a neighbour bumps a counter or every worker is done
             if (threadIdx.x == 0) {
                 atomicSub(&a.hdr->pending, 1);
                 int state = 0;
