@@ -182,3 +182,18 @@ def test_autotune_table_to_opts(tmp_path):
     assert list(o.sub) == [32, 32] and abs(o.stop_margin - 0.95) < 1e-12
     d = at.opts_for(table, 2000)  # class without an entry: defaults
     assert list(d.sub) == [0, 0] and d.stop_margin == 0.0
+
+
+def test_source_digest_ignores_comments_only(tmp_path):
+    """A committed ncu summary stays valid across comment edits of the kernel
+    sources and not across code edits."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = tmp_path / "k.cuh"
+    a.write_text("// header\nint f(int x) {\n    return x + 1;  // one\n}\n/* block\n comment */\n")
+    d0 = bench.source_digest([str(a)])
+    a.write_text("// a reworded header\n\nint f(int x) {\n    return x + 1;  // still one\n}\n")
+    assert bench.source_digest([str(a)]) == d0
+    a.write_text("// header\nint f(int x) {\n    return x + 2;  // one\n}\n")
+    assert bench.source_digest([str(a)]) != d0
+
