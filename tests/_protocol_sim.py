@@ -100,7 +100,7 @@ class Sim:
     arrive the next tick)."""
 
     def __init__(self, pb: Problem, tile, sub, lock=True, schedule="random", seed=0, max_delay=20,
-                 chunks=4, guard=None):
+                 chunks=4, guard=None, workers=None):
         self.pb = pb
         self.t0, self.t1 = (1, tile[0]) if len(tile) == 1 else tile
         self.s0, self.s1 = (1, sub[0]) if len(sub) == 1 else sub
@@ -119,6 +119,12 @@ class Sim:
         self.tick = 0
         self.stop = None     # None, "timeout" or "diverged"
         self.accepted = self.rejected = self.lock_checks = 0
+        # workers < tiles: tiles are scheduled dynamically (see run_dynamic)
+        self.workers = self.G if workers is None else min(int(workers), self.G)
+        self.status = ["queued"] * self.G   # queued / running / idle (dynamic mode)
+        self.ready = list(range(self.G))    # tiles waiting for a worker, in order
+        self.tstate = {}                    # a tile's dirty set, seen counters, m
+        self.activations = 0
         # every accepted border update: |dZ| and the largest competing |dZ|
         # in V(s0) of lower / higher tiles at the time of the test
         self.accept_log = []
@@ -126,7 +132,21 @@ class Sim:
     def tile_of(self, i, j):
         return (i // self.t0) * self.G1 + j // self.t1
 
-    def worker(self, w):
+    def activate(self, w):
+        """An idle tile with news joins the ready queue (dynamic mode)."""
+        if self.status[w] == "idle":
+            self.status[w] = "queued"
+            self.pending += 1
+            self.ready.append(w)
+
+    def worker(self, w, dynamic=False):
+        """Tile w's worker.  Resident (dynamic False): runs until the solve
+        ends, pausing in place.  Dynamic: returns when the tile would pause,
+        leaving it idle (pending - 1) with its state kept for the next
+        worker that takes it -- a notification that reached it meanwhile
+        queues it again -- and also when its candidate is soft-locked, the
+        tile then queued again at once: a worker that kept retrying could
+        wait forever on a blocker whose tile has no worker."""
         pb = self.pb
         ta, tb = divmod(w, self.G1)
         r0, c0 = ta * self.t0, tb * self.t1
@@ -156,8 +176,8 @@ class Sim:
                     out.add(q)
             return out
 
-        dirty = set(range(M))
-        seen, m = {}, 0
+        st = self.tstate.setdefault(w, {"dirty": set(range(M)), "seen": {}, "m": 0})
+        dirty, seen, m = st["dirty"], st["seen"], st["m"]
         while True:
             f_now = dict(self.flag[w])
             yield
@@ -238,10 +258,28 @@ class Sim:
                             dirty.add(q)
                 else:
                     self.rejected += 1
+                    if dynamic:
+                        # the blocker may sit in a tile that waits for a
+                        # worker: give this one up and queue the tile again
+                        # (it stays active), so that every tile gets to run
+                        for d in new:
+                            dirty |= facing(d)
+                        nxt = sorted(q for q in dirty if q > m) or sorted(dirty)
+                        st["m"] = nxt[0]
+                        self.status[w] = "queued"
+                        self.ready.append(w)
+                        return
             else:
                 dirty.discard(m)
             for d in new:
                 dirty |= facing(d)
+            if not dirty and dynamic:
+                st["m"] = m
+                self.status[w] = "idle"
+                self.pending -= 1
+                if any(n != seen.get(d, 0) for d, n in self.flag[w].items()):
+                    self.activate(w)  # a bump it has not seen yet
+                return
             if not dirty:
                 self.pending -= 1
                 while True:
@@ -259,21 +297,43 @@ class Sim:
                     yield
             nxt = sorted(q for q in dirty if q > m) or sorted(dirty)
             m = nxt[0]
+            st["m"] = m
 
     def deliver(self):
         keep = []
         for at, tw, d in self.in_flight:
             if at <= self.tick:
                 self.flag[tw][d] = self.flag[tw].get(d, 0) + 1
+                if self.workers < self.G:
+                    self.activate(tw)  # the sender queues an idle receiver
             else:
                 keep.append([at, tw, d])
         self.in_flight = keep
+
+    def slot(self):
+        """One worker of the dynamic mode: takes the first ready tile, runs
+        it until it would pause, takes the next; ends when no tile is active
+        and no notification is in flight (pending = 0)."""
+        while True:
+            while not self.ready:
+                if self.pending == 0 or self.stop:
+                    return
+                yield
+            w = self.ready.pop(0)
+            self.status[w] = "running"
+            self.activations += 1
+            yield from self.worker(w, dynamic=True)
+            if self.stop:
+                return
 
     def run(self, max_ticks=2_000_000):
         """Runs until every worker has returned.  Returns the tick count; a
         run that reaches max_ticks is stopped ("timeout") like the GPU's
         deadline stops a kernel."""
-        live = {w: self.worker(w) for w in range(self.G)}
+        if self.workers < self.G:
+            live = {q: self.slot() for q in range(self.workers)}
+        else:
+            live = {w: self.worker(w) for w in range(self.G)}
         while live:
             if self.tick >= max_ticks and not self.stop:
                 self.stop = "timeout"

@@ -74,6 +74,36 @@ def test_direction_marking_with_many_sub_domains(orc, w, tile, sub, schedule, se
     assert abs(pb.objective(sim.Z) - f_ref) <= 1e-9 * f_ref
 
 
+DYN_CASES = [(W2, (8, 8), (4, 4), 4, "random", 6, 50), (W2, (8, 11), (4, 4), 3, "lockstep", 0, 1),
+             (W1, (16,), (8,), 5, "random", 7, 100)]
+
+
+@pytest.mark.parametrize("w,tile,sub,workers,schedule,seed,delay", DYN_CASES,
+                         ids=[f"{c[0].name}-{'x'.join(map(str, c[1]))}-{c[3]}workers-{c[4]}{c[5]}"
+                              for c in DYN_CASES])
+def test_dynamic_tile_scheduling_terminates_at_the_optimum(orc, w, tile, sub, workers, schedule, seed, delay):
+    """More tiles than workers: a worker runs a tile until it would pause,
+    leaves it idle with its state (dirty set, seen counters) and takes the
+    next ready one; a notification to an idle tile queues it again.  The
+    termination count (tiles queued or running plus unobserved notifications)
+    still ends the run only at a point where no coordinate can move by eps,
+    and that point is the oracle's optimum."""
+    X, D, _ = make_problem(w, 3)
+    lam = 0.1 * orc.lambda_max(X, D)
+    pb = Problem(X, D, lam, EPS)
+    sim = Sim(pb, tile=tile, sub=sub, lock=True, schedule=schedule, seed=seed, max_delay=delay, workers=workers)
+    assert sim.workers < sim.G
+    sim.run()
+    assert sim.stop is None
+    assert sim.pending == 0 and not sim.in_flight and not sim.ready
+    assert all(st == "idle" for st in sim.status)
+    assert sim.activations > sim.G  # tiles were taken up again after pausing
+    assert pb.kkt(sim.Z) < EPS * (1 + 1e-9)
+    ref = orc.lgcd(X, D, lam, EPS)
+    f_ref = orc.objective(X, D, ref["Z"], lam)
+    assert abs(pb.objective(sim.Z) - f_ref) <= 1e-9 * f_ref
+
+
 def _corner_problem():
     """One 4 x 4 box atom; activations of 5 at every tile corner of a 4 x 4
     tile grid, so the four tiles around a corner all find their best
