@@ -28,6 +28,10 @@ with the sender; a worker whose sub-domains are all clean pauses
 (pending - 1) until a notification arrives (pending + 1) or pending
 reaches 0.
 
+With `workers` below the number of tiles the model also runs a dynamic
+schedule that the GPU does not (yet): workers take ready tiles from a queue,
+a tile that would pause goes idle, and a notification queues an idle tile.
+
 This module is test infrastructure: it shares nothing with the CUDA library."""
 from __future__ import annotations
 
