@@ -12,7 +12,8 @@ notifications not yet observed.  A worker is a generator that yields at every po
 worker may run: after reading its counters, after the scan, after the soft-lock
 test, after writing Z and after each chunk of rows of its window update (so
 neighbours see a half-applied window).  Notifications (counter increments)
-reach their tile after a delay the scheduler draws.
+reach their tile after a delay the scheduler draws, out of order, and with
+`drop` > 0 some deliveries fail and are retried after a fresh delay.
 
 The worker's steps mirror the kernel (paper_1901_09235_gb300/csrc/
 lgcd_global.cuh): scan the dirty sub-domain C_m for the largest
@@ -104,13 +105,16 @@ class Sim:
     arrive the next tick)."""
 
     def __init__(self, pb: Problem, tile, sub, lock=True, schedule="random", seed=0, max_delay=20,
-                 chunks=4, guard=None, workers=None):
+                 chunks=4, guard=None, workers=None, drop=0.0):
         self.pb = pb
         self.t0, self.t1 = (1, tile[0]) if len(tile) == 1 else tile
         self.s0, self.s1 = (1, sub[0]) if len(sub) == 1 else sub
         self.G0, self.G1 = -(-pb.N0 // self.t0), -(-pb.N1 // self.t1)
         self.G = self.G0 * self.G1
         self.lock, self.schedule, self.max_delay, self.chunks = lock, schedule, max_delay, chunks
+        # a delivery attempt fails with this probability and the sender tries
+        # again after a fresh delay (the count it added stays in `pending`)
+        self.drop, self.dropped = float(drop), 0
         self.rng = np.random.default_rng(seed)
         self.guard = guard
         self.beta = pb.beta_init()
@@ -306,7 +310,10 @@ class Sim:
     def deliver(self):
         keep = []
         for at, tw, d in self.in_flight:
-            if at <= self.tick:
+            if at <= self.tick and self.drop > 0 and self.rng.random() < self.drop:
+                self.dropped += 1
+                keep.append([self.tick + 1 + int(self.rng.integers(0, self.max_delay + 1)), tw, d])
+            elif at <= self.tick:
                 self.flag[tw][d] = self.flag[tw].get(d, 0) + 1
                 if self.workers < self.G:
                     self.activate(tw)  # the sender queues an idle receiver

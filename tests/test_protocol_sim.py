@@ -104,6 +104,24 @@ def test_dynamic_tile_scheduling_terminates_at_the_optimum(orc, w, tile, sub, wo
     assert abs(pb.objective(sim.Z) - f_ref) <= 1e-9 * f_ref
 
 
+@pytest.mark.parametrize("workers", [None, 5], ids=["resident", "dynamic"])
+def test_dropped_and_retried_notifications(orc, workers):
+    """A third of the notification deliveries fail and are sent again after a
+    fresh delay: the counts they hold keep the run alive until they land, and
+    it ends at the oracle's optimum."""
+    X, D, _ = make_problem(W2, 4)
+    lam = 0.1 * orc.lambda_max(X, D)
+    pb = Problem(X, D, lam, EPS)
+    sim = Sim(pb, tile=(8, 8), sub=(4, 4), lock=True, schedule="random", seed=8, max_delay=30, workers=workers,
+              drop=0.33)
+    sim.run()
+    assert sim.stop is None and sim.dropped > 0
+    assert sim.pending == 0 and not sim.in_flight
+    assert pb.kkt(sim.Z) < EPS * (1 + 1e-9)
+    ref = orc.lgcd(X, D, lam, EPS)
+    assert abs(pb.objective(sim.Z) - orc.objective(X, D, ref["Z"], lam)) <= 1e-9 * pb.objective(sim.Z)
+
+
 def _corner_problem():
     """One 4 x 4 box atom; activations of 5 at every tile corner of a 4 x 4
     tile grid, so the four tiles around a corner all find their best
