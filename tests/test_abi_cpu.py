@@ -172,3 +172,39 @@ def test_cdl_step_arguments_rejected_on_host(lib):
     assert lib.cdl_step(C.byref(s), *fake[:7], 0.1, 0.0, 1e-4, 1.0, 50, 1e-8, C.byref(bad_opts), fake[7], need,
                         C.byref(st), C.byref(lo), C.byref(fd), C.byref(it), None) == pkg.CSC_ERR_INVALID
     assert call(ws_bytes=1024) == pkg.CSC_ERR_WORKSPACE
+
+
+def test_every_compute_call_refuses_null_buffers_on_the_host(lib):
+    """Each entry point that takes device buffers checks them before any
+    device work: with a valid shape and null buffers it returns
+    CSC_ERR_INVALID (never CSC_ERR_CUDA, which would mean it reached the
+    device first)."""
+    import paper_1901_09235_gb300 as pkg
+    s = pkg.make_shape((2, 40, 40), (3, 2, 5, 5))
+    d, n = C.c_double(0.0), C.c_longlong(0)
+    it = C.c_int(0)
+    st = pkg.SolveStats()
+    o = pkg.default_opts()
+    calls = {
+        "csc_init_beta": lambda: lib.csc_init_beta(C.byref(s), None, None, None, None, None, None, 0, None),
+        "csc_init_beta_f64": lambda: lib.csc_init_beta_f64(C.byref(s), None, None, None, None, None, None, 0,
+                                                           None),
+        "csc_init_beta_bf16x3": lambda: lib.csc_init_beta_bf16x3(C.byref(s), None, None, None, None, None, None,
+                                                                 0, None),
+        "csc_lgcd_solve": lambda: lib.csc_lgcd_solve(C.byref(s), None, None, None, None, None, 0.1, 1e-4,
+                                                     C.byref(o), None, 0, C.byref(st), None),
+        "csc_lgcd_solve_f64": lambda: lib.csc_lgcd_solve_f64(C.byref(s), None, None, None, None, None, 0.1, 1e-4,
+                                                             C.byref(o), None, 0, C.byref(st), None),
+        "csc_objective": lambda: lib.csc_objective(C.byref(s), None, None, None, 0.1, C.byref(d), None, 0, None),
+        "cdl_dict_stats": lambda: lib.cdl_dict_stats(C.byref(s), None, None, None, None, None, 0, None),
+        "cdl_dict_update": lambda: lib.cdl_dict_update(C.byref(s), None, None, 1.0, None, 10, 1e-8, C.byref(d),
+                                                       C.byref(it), None, 0, None),
+        "csc_refresh_beta": lambda: lib.csc_refresh_beta(C.byref(s), None, None, None, 0.1, None, C.byref(d),
+                                                         C.byref(d), None, 0, None),
+        "csc_rcd_solve": lambda: lib.csc_rcd_solve(C.byref(s), None, None, None, None, 0.1, None, 10, C.byref(n),
+                                                   None, 0, None),
+        "csc_sparse_code": lambda: lib.csc_sparse_code(C.byref(s), None, None, None, None, 0, C.byref(n), None,
+                                                       0, None),
+    }
+    for name, call in calls.items():
+        assert call() == pkg.CSC_ERR_INVALID, name
