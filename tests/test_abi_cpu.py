@@ -205,6 +205,8 @@ def test_every_compute_call_refuses_null_buffers_on_the_host(lib):
                                                    None, 0, None),
         "csc_sparse_code": lambda: lib.csc_sparse_code(C.byref(s), None, None, None, None, 0, C.byref(n), None,
                                                        0, None),
+        "cdl_fit": lambda: lib.cdl_fit(C.byref(s), None, None, None, None, None, None, None, 0.1, 1e-4, 2, 0.0,
+                                       10, 1e-8, C.byref(o), None, 0, None, C.byref(it), None),
     }
     for name, call in calls.items():
         assert call() == pkg.CSC_ERR_INVALID, name
